@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the stochastic-LLG Heun step on one node: atomistic spin-steps/s.
+
+Default workload: the batched ensemble of 256 independent simple-cubic grain arrays of
+uneven size (sides 32..96, 8..32 layers, ~2.1e7 sites in total), FP32 state with FP64
+reductions, M(t) recorded every 10 steps, advanced by the fused persistent kernel.  A step
+is one Heun step of every replica.  Beside it: the plain FP64 GPU path on the same workload,
+the end-to-end rate through the C ABI with host buffers, and the FP64 CPU oracle on a
+bounded sample of the same workload (the CPU baseline).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own ensemble (seeds offset by rank, no collective on the
+data path): weak scaling.  Rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE_FP32 = 26   # read S 12 B + write S 12 B + 2-byte grain code
+BYTES_PER_SITE_FP64 = 50   # read S 24 B + write S 24 B + 2-byte grain code
+METRIC = "atomistic spin-steps/s (FP32 batched vs FP64 plain, same GB300)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="ensemble256")
+    p.add_argument("--fp64-steps", type=int, default=30)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([float(v)], device=dev, dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        load = [s for s, p in zip(sm, pw)] if sm else []
+        # samples under load: power above the midpoint of the observed range
+        if pw:
+            cut = min(pw) + 0.5 * (max(pw) - min(pw))
+            load = [s for s, p in zip(sm, pw) if p >= cut] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "samples_under_load": len(load),
+                "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, if it was taken on the
+    kernel source as it is now (else None)."""
+    src = os.path.join(ROOT, "paper_2502_02236_gb300", "csrc", "kernels_fused.cu")
+    path = os.path.join(ROOT, "profiles", "fused_ensemble256_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+        if t.get("kernel_sha256") == h:
+            return t.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def build_lattice(w, precision, rank=0):
+    from paper_2502_02236_gb300 import inputs as I
+    from paper_2502_02236_gb300.hamr import Lattice
+    reps = w["replicas"]
+    seeds = [int(rep["seed"]) ^ (rank << 48) for rep in reps]
+    lat = Lattice([rep["dims"] for rep in reps], seeds, lattice=w["lattice"], precision=precision,
+                  neighbours=w["neighbours"], a=w["a"], c=w["c"], periodic=w["periodic"], mu_s=w["mu_s"],
+                  ku=w["ku"], alpha=w["alpha"], dt=w["dt"])
+    lat.set_neighbour_shells(w["J"])
+    for r, rep in enumerate(reps):
+        if rep.get("grain") is not None:
+            lat.set_grain_map(r, rep["grain"], rep["n_grains"])
+        if rep.get("T"):
+            lat.set_temperature_profile(r, **rep["T"])
+        if rep.get("field"):
+            lat.set_field_sequence(r, **rep["field"])
+    return lat
+
+
+def prime(lat, K, record_every):
+    """Capture, untimed, the CUDA graphs of every block size that a timed call of K steps
+    will replay, and leave the step count aligned to record_every."""
+    if record_every > 0:
+        r = K % record_every
+        if r:
+            lat.sllg_heun_steps(r, record_every)
+            lat.sllg_heun_steps(record_every - r, record_every)
+    else:
+        lat.sllg_heun_steps(64 + K % 64, 0)
+
+
+def timed(lat, dist, K, record_every):
+    import torch
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lat.sllg_heun_steps_async(K, record_every)
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    lat.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def cpu_baseline(w, seconds, steps_cap=None):
+    """The FP64 oracle as it stands on this host's cores, over a bounded sample of the
+    workload: whole replicas in order, one step at a time, until `seconds` have passed."""
+    import oracle as orc
+    from paper_2502_02236_gb300 import inputs as I
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from common import initial, oracle_params
+    done_sites = 0
+    steps = 0
+    used = []
+    t0 = time.perf_counter()
+    for r, rep in enumerate(w["replicas"]):
+        o = orc.Oracle(oracle_params(w, r), rep.get("grain"))
+        S = initial(rep)
+        n = int(np.prod(rep["dims"]))
+        o.step(S, 0)
+        done_sites += n
+        steps += 1
+        used.append(r)
+        if time.perf_counter() - t0 > seconds or (steps_cap and steps >= steps_cap):
+            break
+    el = time.perf_counter() - t0
+    return done_sites / el, used, el
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        return reference_arm(args, dist)
+    import torch
+    from paper_2502_02236_gb300 import build
+    from paper_2502_02236_gb300 import inputs as I
+    if dist.rank == 0:
+        build.build()
+    dist.barrier()
+    build.build()
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)     # the library runs on (and is timed on) this stream
+    W = max(3, args.warmup)
+    K = args.steps
+    w = I.workload(args.workload)
+    rec = int(w.get("record_every", 10))
+    n_sites = sum(int(np.prod(rep["dims"])) for rep in w["replicas"])
+    n_mag = sum(int((np.asarray(rep["grain"]) >= 0).sum()) if rep.get("grain") is not None
+                else int(np.prod(rep["dims"])) for rep in w["replicas"])
+
+    lat = build_lattice(w, "fp32", dist.rank)
+    tile = lat.autotune(5)
+    lat.sllg_heun_steps(W - W % rec + rec, rec)
+    prime(lat, K, rec)
+    prime(lat, K, 0)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    ms = timed(lat, dist, K, rec)
+    clk = clocks.stop()
+    ms = dist.max(ms)
+    value = n_sites * K * dist.world / (ms / 1e3)
+    # the dominant kernel alone: the same K steps without records (one fused launch per step
+    # plus one bookkeeping launch per 64 steps)
+    ms_k = dist.max(timed(lat, dist, K, 0))
+    t_launch = ms_k / K / 1e3
+    achieved = BYTES_PER_SITE_FP32 * n_sites / t_launch / 1e9
+    peak, peak_kind = peaks()
+    assert lat.check_finite()
+    launches = K + K // rec
+
+    out = {"metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": dist.world, "steps": K,
+           "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "replicas": len(w["replicas"]), "lattice_sites": n_sites,
+                      "magnetic_sites": n_mag, "record_every": rec, "tile": list(tile),
+                      "l2": "inputs larger than L2 (two %.0f MB FP32 state buffers)" % (12 * n_sites / 1e6),
+                      "parallelism": "replica batches per GPU, no collective"},
+           "magnetic_spin_steps_per_s": n_mag * K * dist.world / (ms / 1e3),
+           "gpu_launches": launches,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": kernel_traffic(),
+                        "peak_source": peak_kind, "kernel": "k_fused", "avg_launch_ms": t_launch * 1e3,
+                        "bytes_per_site": BYTES_PER_SITE_FP32},
+           "clocks": clk}
+
+    # plain FP64 path on the same workload (the speedup denominator)
+    if not args.no_fp64:
+        lat64 = build_lattice(w, "fp64", dist.rank)
+        K64 = max(1, args.fp64_steps)
+        lat64.sllg_heun_steps(rec, rec)
+        prime(lat64, K64, rec)
+        ms64 = dist.max(timed(lat64, dist, K64, rec))
+        v64 = n_sites * K64 * dist.world / (ms64 / 1e3)
+        out["fp64_plain"] = {"value": v64, "unit": "spin-steps/s", "steps": K64, "ms_per_step": ms64 / K64,
+                             "launches_per_step": 2, "dtype": "f64"}
+        out["speedup_fp32_over_fp64"] = value / v64
+        lat64.close()
+
+    # end to end through the C ABI with host buffers: upload all spins from pinned memory,
+    # K steps with records, read the records and all spins back
+    if not args.no_e2e:
+        S_host = [torch.empty((int(np.prod(rep["dims"])), 3), dtype=torch.float64).pin_memory()
+                  for rep in w["replicas"]]
+        for t in S_host:
+            t[:, 2] = 1.0
+        hb = sum(t.numel() * 8 for t in S_host)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r, t in enumerate(S_host):
+            lat.set_moments(r, t.numpy())
+        lat.sllg_heun_steps(K, rec)
+        d2h = 0
+        for r, t in enumerate(S_host):
+            M, st, _ = lat.read_magnetisation(r)
+            d2h += M.nbytes
+            lat.read_moments(r, t.numpy())
+        el = dist.max(time.perf_counter() - t0)
+        d2h += hb
+        out["e2e"] = {"value": n_sites * K * dist.world / el, "unit": "spin-steps/s",
+                      "h2d_bytes_per_step": hb / K, "d2h_bytes_per_step": d2h / K,
+                      "note": "per call: H2D of all spins, K steps, D2H of M(t) and all spins; bytes / K"}
+
+    if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        v, used, el = cpu_baseline(w, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "spin-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": "one FP64 oracle step of replicas 0..%d of the workload (%.1f s)"
+                                         % (used[-1], el)}
+    lat.close()
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+
+
+def reference_arm(args, dist):
+    """The FP64 CPU oracle timed on this host's cores on the same workload, metric and unit."""
+    if dist.rank != 0:
+        dist.close()
+        return
+    from paper_2502_02236_gb300 import inputs as I
+    import oracle as orc
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from common import initial, oracle_params
+    w = I.workload(args.workload)
+    # sample: the first replicas of the ensemble up to ~3e5 sites, stepped K + W times
+    reps, n = [], 0
+    for r, rep in enumerate(w["replicas"]):
+        reps.append(r)
+        n += int(np.prod(rep["dims"]))
+        if n >= 300000:
+            break
+    orcs = [orc.Oracle(oracle_params(w, r), w["replicas"][r].get("grain")) for r in reps]
+    S = [initial(w["replicas"][r]) for r in reps]
+    W, K = max(3, args.warmup), args.steps
+    budget = 150.0
+    t_start = time.perf_counter()
+    for k in range(min(W, 3)):
+        for o, s in zip(orcs, S):
+            o.step(s, k)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(K):
+        for o, s in zip(orcs, S):
+            o.step(s, W + k)
+        done += 1
+        if time.perf_counter() - t_start > budget:
+            break
+    el = time.perf_counter() - t0
+    v = n * done / el
+    out = {"metric": METRIC, "value": v, "unit": "spin-steps/s", "n_gpus": dist.world, "steps": done,
+           "warmup": W, "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "sample_replicas": len(reps), "sample_sites": n},
+           "cpu_baseline": {"value": v, "unit": "spin-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "replicas 0..%d (%d sites), %d steps" % (reps[-1], n, done)},
+           "e2e": {"value": v, "unit": "spin-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

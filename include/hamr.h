@@ -1,0 +1,224 @@
+/*
+ * hamr.h -- C ABI of the GB300 stochastic-LLG library.
+ *
+ * One library call advances the atomistic spin lattice of the laser-heated write
+ * window of a HAMR model (arXiv 2502.02236) by Heun steps of the stochastic
+ * Landau-Lifshitz-Gilbert equation (Sec. II, Eq. 1), with
+ *   - exchange from a neighbour list: simple cubic, 6 nearest neighbours, or the L1_0
+ *     FePt Fe sublattice, 4 nearest + 6 next-nearest neighbours in up to 3 shells
+ *     (Sec. II, Eq. 2; Appendix A);
+ *   - uniaxial anisotropy along z (Eq. 3);
+ *   - a spatially uniform write field whose polarity follows a bit pattern (Sec. III);
+ *   - a thermal field, Gaussian with standard deviation
+ *     sqrt(2 alpha kB T_i / (gamma mu_s dt)) (Sec. II, text under Eq. 1), where T_i is the
+ *     local temperature of a Gaussian laser spot moving at constant velocity (Sec. III);
+ * and FP64 reductions of the magnetisation, total and per grain (Eq. 6 as an average).
+ *
+ * Units: SI, fields in tesla (B = mu0 H), so gamma is in rad/(s T) and the thermal
+ * standard deviation above is in tesla.  Equation of motion, per site i:
+ *   dS/dt = -gamma/(1+alpha^2) [S x B + alpha S x (S x B)],
+ *   B = (1/mu_s) sum_j J_ij S_j + (2 ku/mu_s)(S.z) z + B_app(t) + B_th,i.
+ * One step from t_n = n dt (drivers frozen at t_n, the same thermal field in both stages):
+ *   S'    = N(S + dt f(S, B(S)))
+ *   S_new = N(S + dt/2 [f(S, B(S)) + f(S', B(S'))]),   N(v) = v/|v|.
+ * Thermal normals: Philox4x32-10 (Salmon et al., SC'11) with key = the replica's 64-bit
+ * seed (low word, high word) and counter = (site low, site high, step low, step high),
+ * site = ix + nx (iy + ny iz); u_k = (x_k + 1/2) 2^-32; Box-Muller on (u0, u1) gives the x
+ * and y normals, on (u2, u3) the z normal.  Results therefore do not depend on how the
+ * lattice is tiled or batched.
+ *
+ * Conventions for every call:
+ *   - Return value: HAMR_OK (0) or a negative hamr_status; no call aborts or throws.
+ *     hamr_last_error(h) then describes the failure; the handle stays usable unless the
+ *     status is HAMR_ERR_CUDA after a device fault.
+ *   - Host arrays passed in are copied before the call returns; the caller keeps
+ *     ownership.  Output arrays are caller-allocated.
+ *   - Spin arrays at the boundary are FP64, site-major with three components
+ *     (AoS: S[3*i + d]), sites ordered x fastest, then y, then z, whatever the internal
+ *     precision.
+ *   - Calls run on the stream given at creation and return when their work is done
+ *     (host-synchronous), except where stated.
+ *   - Non-magnetic sites (grain id -1) hold S = 0, are never updated and do not count
+ *     in any average.
+ */
+#ifndef HAMR_H
+#define HAMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hamr_ctx *hamr_t;
+
+typedef enum {
+    HAMR_OK = 0,
+    HAMR_ERR_ARG = -1,      /* invalid argument; nothing was changed */
+    HAMR_ERR_OOM = -2,      /* device or host allocation failed */
+    HAMR_ERR_CUDA = -3,     /* a CUDA call failed (message names it) */
+    HAMR_ERR_STATE = -4,    /* call out of order (e.g. step before the exchange is set) */
+    HAMR_ERR_TIMEOUT = -5,  /* a bounded device wait ran out */
+    HAMR_ERR_NUMERIC = -6,  /* NaN or Inf found in the spin state */
+    HAMR_ERR_IO = -7        /* file could not be read or written, or is malformed */
+} hamr_status;
+
+enum { HAMR_LATTICE_SC = 0, HAMR_LATTICE_L10 = 1 };
+enum { HAMR_FP32 = 0, HAMR_FP64 = 1 };
+enum { HAMR_NBR_STENCIL = 0, HAMR_NBR_CSR = 1 };
+
+typedef struct {
+    int32_t lattice;      /* HAMR_LATTICE_SC: sites at ((i+1/2)a, (j+1/2)a, (k+1/2)a).
+                             HAMR_LATTICE_L10: Fe sublattice of the L1_0 fct cell (a, c):
+                             square nets of spacing a/sqrt(2) stacked at c, sites at
+                             ((i+1/2)a/sqrt2, (j+1/2)a/sqrt2, (k+1/2)c) (Appendix A). */
+    int32_t precision;    /* HAMR_FP32: spin state and field arithmetic in FP32, FP64
+                             reductions.  HAMR_FP64: everything in FP64. */
+    int32_t neighbours;   /* HAMR_NBR_STENCIL: implicit 6-neighbour stencil (SC only).
+                             HAMR_NBR_CSR: neighbour list, built from the geometry at
+                             creation or replaced per replica by hamr_set_csr. */
+    int32_t n_replicas;   /* independent lattices advanced together, >= 1 */
+    const int32_t *dims;  /* [3 * n_replicas]: nx, ny, nz of each replica, each >= 1 */
+    const uint64_t *seeds;/* [n_replicas]: Philox key of each replica */
+    double a;             /* SC spacing, or the L1_0 in-plane fct constant [m], > 0 */
+    double c;             /* L1_0 fct constant along z [m]; ignored for SC */
+    int32_t periodic[3];  /* periodic boundary along x, y, z (0 = open) */
+    double mu_s;          /* atomic moment [J/T], > 0 */
+    double ku;            /* uniaxial anisotropy energy per atom [J] (K_1 of Eq. 3) */
+    double alpha;         /* damping, the paper's lambda, >= 0 */
+    double dt;            /* time step [s], > 0 */
+    double gamma;         /* gyromagnetic ratio [rad/(s T)], > 0 */
+    int32_t device;       /* CUDA device ordinal */
+    void *stream;         /* cudaStream_t for all work of this handle.  NULL: the library
+                             creates its own non-blocking stream (the legacy default stream
+                             cannot be captured into CUDA graphs); callers that pass device
+                             pointers must then order their own work with it. */
+} hamr_lattice_desc;
+
+/* Create a handle: allocates device state for all replicas (all spins +z, every site
+ * magnetic and in grain 0, T = 0, no field, step counter 0).  *out is set on success and
+ * owned by the caller until hamr_destroy.  Errors: ARG (bad descriptor), OOM, CUDA. */
+int hamr_lattice_create(hamr_t *out, const hamr_lattice_desc *d);
+
+/* Exchange energies J_s [J] of the neighbour shells (Eq. 2; Eq. 8 relates J to T_C).
+ * SC: n_shells = 1 (bond length a).  L1_0: n_shells = 3, bond lengths a/sqrt2 (4 in-plane
+ * nearest), c (2 out of plane) and a (4 in-plane diagonals); the paper uses one J for all
+ * ten.  Must be called before the first step.  Errors: ARG. */
+int hamr_set_neighbour_shells(hamr_t h, int32_t n_shells, const double *J);
+
+/* Replace the neighbour list of one replica (HAMR_NBR_CSR only): row_ptr[n+1], col[nnz]
+ * site indices of that replica (x fastest), shell[nnz] in [0, n_shells).  At most 32
+ * neighbours per site.  Bonds touching a non-magnetic site are ignored.  Bonds must be
+ * symmetric for energy conservation but this is not checked.  Errors: ARG, STATE
+ * (stencil handle), OOM. */
+int hamr_set_csr(hamr_t h, int32_t replica, const int32_t *row_ptr, const int32_t *col,
+                 const uint8_t *shell);
+
+/* Grain map of one replica (Sec. II: exchange-decoupled grains): grain[n] with ids in
+ * [0, n_grains) or -1 for a non-magnetic site.  Exchange bonds join only sites of the
+ * same grain; spins of non-magnetic sites are set to 0.  n_grains <= 65534.
+ * Errors: ARG. */
+int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t n_grains);
+
+/* Laser temperature of one replica (Sec. III, Fig. 2):
+ * T(x, y, t) = T_amb + (T_peak - T_amb) exp(-4 ln2 [(x - x0 - vx t)^2 + (y - y0 - vy t)^2] / fwhm^2),
+ * uniform in z; fwhm <= 0 gives the uniform T_amb.  Kelvin, metres, m/s.  Errors: ARG
+ * (negative temperature). */
+int hamr_set_temperature_profile(hamr_t h, int32_t replica, double T_amb, double T_peak,
+                                 double fwhm, double x0, double y0, double vx, double vy);
+
+/* Write field of one replica (Sec. III): B_app(t) = B0 s(t) dir, where the head at
+ * x_h = head_x0 + head_v t sits in bit b = floor(x_h / bit_len) and s ramps linearly from
+ * the polarity of bit b-1 to that of bit b over the first ramp_len of bit b (bit 1 ->
+ * polarity -1, bit 0 -> +1; before the first bit and after the last the end bits hold).
+ * n_bits = 0 gives the static field B0 dir.  dir is used as given (not normalised).
+ * Errors: ARG. */
+int hamr_set_field_sequence(hamr_t h, int32_t replica, double B0, const double dir[3],
+                            const uint8_t *bits, int32_t n_bits, double bit_len,
+                            double ramp_len, double head_x0, double head_v);
+
+/* Spin state of one replica from host memory, S[3n] FP64 AoS (converted to the handle's
+ * precision; non-magnetic sites are stored as 0).  Errors: ARG, CUDA. */
+int hamr_set_moments(hamr_t h, int32_t replica, const double *S);
+
+/* As hamr_set_moments, from device memory on the handle's device (S_dev[3n] FP64 AoS);
+ * stream-ordered, returns without waiting. */
+int hamr_set_moments_device(hamr_t h, int32_t replica, const double *S_dev);
+
+/* Advance every replica by n_steps Heun steps (n_steps >= 0).  With record_every > 0 the
+ * magnetisation of each replica is recorded after every completed step whose global
+ * count is a multiple of record_every, and per-grain sums are kept for the latest
+ * record.  Steps run as CUDA-graph replays of record_every steps (or 64 without
+ * records).  Errors: STATE (exchange not set), CUDA, TIMEOUT, NUMERIC (only when
+ * hamr_check_finite finds a bad value). */
+int hamr_sllg_heun_steps(hamr_t h, int64_t n_steps, int32_t record_every);
+
+/* As hamr_sllg_heun_steps but stream-ordered: returns after enqueueing the work. Records
+ * become readable after hamr_synchronize. */
+int hamr_sllg_heun_steps_async(hamr_t h, int64_t n_steps, int32_t record_every);
+
+/* Wait for all work of the handle; moves pending records to the host record list. */
+int hamr_synchronize(hamr_t h);
+
+/* Spin state of one replica to host memory, S_out[3n] FP64 AoS.  Errors: ARG, CUDA. */
+int hamr_read_moments(hamr_t h, int32_t replica, double *S_out);
+
+/* As hamr_read_moments, into device memory S_dev[3n] on the handle's device;
+ * stream-ordered, returns without waiting. */
+int hamr_read_moments_device(hamr_t h, int32_t replica, double *S_dev);
+
+/* Magnetisation records of one replica since creation or hamr_clear_records: M_t gets up
+ * to `capacity` records of 3 doubles (M = sum over magnetic sites of S / their number),
+ * *n_rec the number available (call with M_t = NULL to size the buffer).  M_grain, if not
+ * NULL, gets n_grains x 3 doubles: each grain's average spin at the latest record.
+ * step_of_rec, if not NULL, gets the completed-step count of each returned record.
+ * Errors: ARG. */
+int hamr_read_magnetisation(hamr_t h, int32_t replica, double *M_t, int64_t capacity,
+                            int64_t *n_rec, double *M_grain, int64_t *step_of_rec);
+
+/* Forget all stored records. */
+int hamr_clear_records(hamr_t h);
+
+/* Energy of one replica at the current state and step [J]:
+ * E = -1/2 sum_i sum_j J_ij S_i.S_j - sum_i ku (S_i.z)^2 - sum_i mu_s B_app(t).S_i,
+ * accumulated in FP64.  Errors: ARG, STATE, CUDA. */
+int hamr_read_energy(hamr_t h, int32_t replica, double *E);
+
+/* Count of completed steps (the n of t_n = n dt for the next step). */
+int hamr_get_step(hamr_t h, int64_t *step);
+int hamr_set_step(hamr_t h, int64_t step);
+
+/* Scan the spin state for NaN/Inf (and |S| far from 1 on magnetic sites).  Returns
+ * HAMR_OK or HAMR_ERR_NUMERIC. */
+int hamr_check_finite(hamr_t h);
+
+/* Checkpoint: spins, step counter, seeds and lattice shape to a binary file.  Because the
+ * thermal field is counter-based, a run resumed from a checkpoint is bitwise identical to
+ * an uninterrupted one.  Load requires a handle of the same shape and precision.
+ * Errors: IO, ARG, CUDA. */
+int hamr_save_state(hamr_t h, const char *path);
+int hamr_load_state(hamr_t h, const char *path);
+
+/* Tile shape of the fused FP32 stencil kernel: threads tx * ty cover a (tx-2) x (ty-2)
+ * block of columns plus a one-site halo.  hamr_autotune times the compiled shapes on the
+ * current state (advancing nothing: state and step are restored) and keeps the fastest.
+ * hamr_get_tile reports the shape in use.  Errors: ARG (shape not compiled), CUDA. */
+int hamr_set_tile(hamr_t h, int32_t tx, int32_t ty);
+int hamr_get_tile(hamr_t h, int32_t *tx, int32_t *ty);
+int hamr_autotune(hamr_t h, int32_t steps_per_trial);
+
+/* Sizes: key 0 = total lattice sites, 1 = magnetic sites, 2 = device bytes held,
+ * 3 = kernel launches per step (excluding records), 4 = storage slots. */
+int hamr_query(hamr_t h, int32_t key, int64_t *value);
+
+/* Message of the last failed call on this handle (never NULL). */
+const char *hamr_last_error(hamr_t h);
+
+/* Free all device and host memory of the handle.  NULL is allowed. */
+void hamr_destroy(hamr_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAMR_H */

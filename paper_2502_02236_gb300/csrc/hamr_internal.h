@@ -1,0 +1,194 @@
+// Internal types of the GB300 sLLG library: device-side replica table, physical
+// constants, kernel argument blocks and the host context behind a hamr_t.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hamr.h"
+
+namespace hamr {
+
+constexpr double KB = 1.380649e-23;   // Boltzmann constant [J/K]
+constexpr int SLOT_ALIGN = 256;       // replica storage offsets are multiples of this
+constexpr int PLAIN_BLOCK = 256;      // threads per block of the two-pass kernels
+constexpr int MAX_SHELLS = 4;
+constexpr int ELL_MAX = 32;           // neighbours per site in the list format
+constexpr int ELL_SHELL_SHIFT = 28;   // packed neighbour: storage index | shell << 28
+
+// Per-replica constants, read by every kernel (one entry per replica in device memory).
+struct ReplicaDev {
+    int nx, ny, nz, px;        // logical dimensions and storage pitch along x
+    long long off;             // storage slot of site (0,0,0)
+    long long n;               // nx * ny * nz
+    unsigned key0, key1;       // Philox key = replica seed (low, high)
+    int grain_off, n_grains;   // this replica's grain bins in the global accumulator
+    int cross_grain;           // 1 when a stencil bond joins two different grains
+    int n_bits, bits_off;      // write-field bit pattern in the global bit buffer
+    int pad_;
+    // laser spot: T = T_amb + dT exp(c_fwhm r^2), c_fwhm = -4 ln2 / fwhm^2 (0: uniform)
+    double T_amb, dT, c_fwhm, x0, y0, vx, vy;
+    // write field B0 * s(t) * dir
+    double B0, dir[3], bit_len, ramp_len, head_x0, head_v;
+    // FP32 copies used by the FP32 kernels
+    float fT_amb, fdT, fc_fwhm, fx0, fy0, fvx, fvy;
+    float fB0, fdir[3], fbit_len, framp_len, fhead_x0, fhead_v;
+};
+
+// Constants shared by all replicas.
+struct Phys {
+    double cJ[MAX_SHELLS];  // J_s / mu_s [T]
+    double cK;              // 2 ku / mu_s [T]
+    double pref;            // -gamma / (1 + alpha^2)
+    double alpha, dt;
+    double sig0;            // sqrt(2 alpha kB / (gamma mu_s dt)); sigma_i = sig0 sqrt(T_i) [T]
+    double ax, ay, az;      // site spacing [m]
+    int per[3];
+    int n_shells;
+};
+
+// Device control block.
+struct Ctl {
+    long long step;          // completed steps
+    long long n_rec;         // records written since the host last collected them
+    unsigned work_ctr[2];    // work-list counters of the persistent kernel (by step parity)
+    int err;                 // error flags (bit 0: bad value found by the finite check)
+    int pad_;
+};
+
+// One unit of work of the fused kernel: a block of columns of one replica.
+struct WorkItem {
+    int r;        // replica
+    int x0, y0;   // first interior column
+    int bxy;      // interior width | height << 16
+};
+
+template <typename Real>
+struct PlainArgs {
+    Real *S, *SP, *F1, *BTH;      // component planes [3][NS]
+    long long NS;
+    const uint16_t *gcode;        // grain code per slot: 0 = non-magnetic, else grain + 1
+    const int *blk_rep;           // replica of each PLAIN_BLOCK-slot block
+    const ReplicaDev *reps;
+    const uint8_t *bits;
+    const int *ell;               // packed neighbour list [ell_w][NS], or null (stencil)
+    int ell_w;
+    const Ctl *ctl;
+    int step_off;
+    Phys ph;
+    double *grain_acc;            // [G][3] sums at record steps
+};
+
+struct FusedArgs {
+    float *Sbuf0, *Sbuf1;       // state at step n lives in Sbuf[n & 1]
+    long long NS;
+    const uint16_t *gcode;
+    const ReplicaDev *reps;
+    const uint8_t *bits;
+    const WorkItem *items;
+    int n_items;
+    Ctl *ctl;
+    int step_off;
+    float cJ, cK, pref, alpha, dt, sig0, ax, ay, az;
+    int per[3];
+    double *grain_acc;
+};
+
+// kernel launchers (kernels_*.cu)
+cudaError_t launch_plain_step(int prec, const void *args, int n_blocks, bool record, cudaStream_t st);
+cudaError_t launch_fused_step(int tx, int ty, const FusedArgs &a, int grid, bool record, cudaStream_t st);
+bool fused_shape_compiled(int tx, int ty);
+int fused_max_blocks_per_sm(int tx, int ty);
+void fused_shapes(std::vector<std::pair<int, int>> &out);
+cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps,
+                               const long long *nmag, const long long *gcount, int Gtot, double *grain_acc,
+                               double *grain_last, double *rec, long long rec_cap,
+                               long long *rec_step, cudaStream_t st);
+cudaError_t launch_init_state(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
+cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
+cudaError_t launch_aos_to_soa(int prec, const double *src, void *S, long long NS, const ReplicaDev *reps,
+                              int r, const uint16_t *gcode, long long n, cudaStream_t st);
+cudaError_t launch_soa_to_aos(int prec, const void *S, long long NS, const ReplicaDev *reps, int r,
+                              double *dst, long long n, cudaStream_t st);
+cudaError_t launch_energy(int prec, const void *S, long long NS, const uint16_t *gcode,
+                          const ReplicaDev *reps, const ReplicaDev &Rh, int r, const uint8_t *bits,
+                          const int *ell, int ell_w, const Phys &ph, long long step, double ku, double mu_s,
+                          double *out, cudaStream_t st);
+cudaError_t launch_check_finite(int prec, const void *S, long long NS, const uint16_t *gcode, Ctl *ctl,
+                                cudaStream_t st);
+cudaError_t launch_copy_state(int prec, const void *src, void *dst, long long NS, cudaStream_t st);
+
+}  // namespace hamr
+
+// The host context behind a hamr_t.
+struct hamr_ctx {
+    std::string err;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int lattice = 0, prec = 0, nbr = 0, R = 0;
+    std::vector<int> dims;            // 3R
+    std::vector<uint64_t> seeds;
+    double a = 0, c = 0, mu_s = 0, ku = 0, alpha = 0, dt = 0, gamma = 0;
+    int per[3] = {0, 0, 0};
+    hamr::Phys ph{};
+    bool shells_set = false;
+    std::vector<double> J;
+
+    long long NS = 0;                 // storage slots per component
+    std::vector<hamr::ReplicaDev> reps_h;
+    hamr::ReplicaDev *reps_d = nullptr;
+    void *S[2] = {nullptr, nullptr};  // state planes [3][NS] (FP32 fused path ping-pongs)
+    int cur = 0;
+    void *SP = nullptr, *F1 = nullptr, *BTH = nullptr;   // two-pass intermediates
+    uint16_t *gcode_d = nullptr;
+    std::vector<uint16_t> gcode_h;
+    int *blk_rep_d = nullptr;
+    int *ell_d = nullptr;
+    int ell_w = 0;
+    std::vector<int> ell_h;           // host copy of the packed list (rebuilt per replica)
+    // user-supplied lists (logical site indices), kept to re-filter when grains change
+    std::vector<std::vector<int>> ucsr_rp, ucsr_col;
+    std::vector<std::vector<uint8_t>> ucsr_sh;
+    int max_user_shell = -1;
+    uint8_t *bits_d = nullptr;
+    std::vector<std::vector<uint8_t>> bits_h;
+    size_t bits_cap = 0;
+    hamr::Ctl *ctl_d = nullptr;
+
+    // reductions
+    std::vector<int> n_grains;        // per replica
+    int G = 0, G_cap = 0;             // total grain bins and allocated capacity
+    double *grain_acc_d = nullptr, *grain_last_d = nullptr;
+    long long *gcount_d = nullptr, *nmag_d = nullptr;
+    std::vector<long long> gcount_h, nmag_h;
+    std::vector<std::vector<long long>> gcount_rep;   // per replica, per grain
+    double *rec_d = nullptr;
+    long long *rec_step_d = nullptr;
+    long long rec_cap = 0;
+    std::vector<double> rec_h;        // [n][R][3]
+    std::vector<long long> rec_step_h;
+    std::vector<double> grain_last_h;
+    bool pending_records = false;
+    double *dscratch_d = nullptr;     // small FP64 scratch (energy)
+    double *stage_d = nullptr;        // FP64 AoS staging for host copies (3 x max replica)
+    long long stage_n = 0;
+    long long step_h = 0;             // host mirror of the step counter
+
+    // fused kernel tiling
+    int tile_tx = 32, tile_ty = 8;
+    hamr::WorkItem *items_d = nullptr;
+    int n_items = 0, items_cap = 0;
+    int fused_grid = 0;
+    bool items_dirty = true;
+    int num_sms = 0;
+    size_t dev_bytes = 0;
+
+    // captured step blocks: (steps, record, start parity, tile) -> executable graph
+    std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
+};

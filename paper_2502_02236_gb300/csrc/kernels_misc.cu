@@ -1,0 +1,163 @@
+// Record bookkeeping after a block of steps, layout conversion between the FP64 site-major
+// boundary format and the internal component planes, state initialisation and the
+// finite-value scan.
+#include "device_common.cuh"
+
+namespace hamr {
+
+// After a block of G steps: advance the step counter and, at a record point, turn the
+// per-grain FP64 sums into the replica magnetisation M = sum S / N_mag (Eq. 6 as an
+// average over magnetic sites), per-grain averages, and clear the sums.
+__global__ void k_bookkeeping(Ctl *ctl, int G, int record, int R, const ReplicaDev *reps, const long long *nmag,
+                              const long long *gcount, int Gtot, double *grain_acc, double *grain_last,
+                              double *rec, long long rec_cap, long long *rec_step) {
+    const long long after = ctl->step + G;
+    if (record) {
+        const long long idx = ctl->n_rec;
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+            const int g0 = reps[r].grain_off, ng = reps[r].n_grains;
+            double mx = 0, my = 0, mz = 0;
+            for (int g = g0; g < g0 + ng; ++g) {
+                mx += grain_acc[3 * g];
+                my += grain_acc[3 * g + 1];
+                mz += grain_acc[3 * g + 2];
+            }
+            const double nm = (double)nmag[r];
+            if (idx < rec_cap) {
+                double *o = rec + (idx * R + r) * 3;
+                o[0] = nm > 0 ? mx / nm : 0.0;
+                o[1] = nm > 0 ? my / nm : 0.0;
+                o[2] = nm > 0 ? mz / nm : 0.0;
+            }
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < Gtot; g += blockDim.x) {
+            const double c = (double)gcount[g];
+            for (int d = 0; d < 3; ++d) {
+                grain_last[3 * g + d] = c > 0 ? grain_acc[3 * g + d] / c : 0.0;
+                grain_acc[3 * g + d] = 0.0;
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (idx < rec_cap) rec_step[idx] = after;
+            ctl->n_rec = idx + 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl->step = after;
+}
+
+cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps, const long long *nmag,
+                               const long long *gcount, int Gtot, double *grain_acc, double *grain_last,
+                               double *rec, long long rec_cap, long long *rec_step, cudaStream_t st) {
+    k_bookkeeping<<<1, 256, 0, st>>>(ctl, G, record ? 1 : 0, R, reps, nmag, gcount, Gtot, grain_acc, grain_last,
+                                     rec, rec_cap, rec_step);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+__global__ void k_aos_to_soa(const double *src, Real *S, long long NS, const ReplicaDev *reps, int r,
+                             const uint16_t *gcode, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ReplicaDev &R = reps[r];
+    const long long x = i % R.nx, yz = i / R.nx, y = yz % R.ny, z = yz / R.ny;
+    const long long j = R.off + x + R.px * (y + R.ny * z);
+    const bool mag = gcode[j] != 0;
+    S[j] = mag ? (Real)src[3 * i] : Real(0);
+    S[NS + j] = mag ? (Real)src[3 * i + 1] : Real(0);
+    S[2 * NS + j] = mag ? (Real)src[3 * i + 2] : Real(0);
+}
+
+template <typename Real>
+__global__ void k_soa_to_aos(const Real *S, long long NS, const ReplicaDev *reps, int r, double *dst, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ReplicaDev &R = reps[r];
+    const long long x = i % R.nx, yz = i / R.nx, y = yz % R.ny, z = yz / R.ny;
+    const long long j = R.off + x + R.px * (y + R.ny * z);
+    dst[3 * i] = (double)S[j];
+    dst[3 * i + 1] = (double)S[NS + j];
+    dst[3 * i + 2] = (double)S[2 * NS + j];
+}
+
+template <typename Real>
+__global__ void k_init_state(Real *S, long long NS, const uint16_t *gcode) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NS) return;
+    S[j] = Real(0);
+    S[NS + j] = Real(0);
+    S[2 * NS + j] = gcode[j] ? Real(1) : Real(0);
+}
+
+template <typename Real>
+__global__ void k_zero_void(Real *S, long long NS, const uint16_t *gcode) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NS || gcode[j] != 0) return;
+    S[j] = Real(0);
+    S[NS + j] = Real(0);
+    S[2 * NS + j] = Real(0);
+}
+
+template <typename Real>
+__global__ void k_check_finite(const Real *S, long long NS, const uint16_t *gcode, Ctl *ctl) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NS || gcode[j] == 0) return;
+    const double x = S[j], y = S[NS + j], z = S[2 * NS + j];
+    const double n2 = x * x + y * y + z * z;
+    if (!isfinite(n2) || fabs(n2 - 1.0) > 1e-3) atomicOr(&ctl->err, 1);
+}
+
+static unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_aos_to_soa(int prec, const double *src, void *S, long long NS, const ReplicaDev *reps, int r,
+                              const uint16_t *gcode, long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (prec == HAMR_FP64)
+        k_aos_to_soa<double><<<nblk(n, 256), 256, 0, st>>>(src, (double *)S, NS, reps, r, gcode, n);
+    else
+        k_aos_to_soa<float><<<nblk(n, 256), 256, 0, st>>>(src, (float *)S, NS, reps, r, gcode, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soa_to_aos(int prec, const void *S, long long NS, const ReplicaDev *reps, int r, double *dst,
+                              long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (prec == HAMR_FP64)
+        k_soa_to_aos<double><<<nblk(n, 256), 256, 0, st>>>((const double *)S, NS, reps, r, dst, n);
+    else
+        k_soa_to_aos<float><<<nblk(n, 256), 256, 0, st>>>((const float *)S, NS, reps, r, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st) {
+    if (prec == HAMR_FP64)
+        k_init_state<double><<<nblk(NS, 256), 256, 0, st>>>((double *)S, NS, gcode);
+    else
+        k_init_state<float><<<nblk(NS, 256), 256, 0, st>>>((float *)S, NS, gcode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st) {
+    if (prec == HAMR_FP64)
+        k_zero_void<double><<<nblk(NS, 256), 256, 0, st>>>((double *)S, NS, gcode);
+    else
+        k_zero_void<float><<<nblk(NS, 256), 256, 0, st>>>((float *)S, NS, gcode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(int prec, const void *S, long long NS, const uint16_t *gcode, Ctl *ctl,
+                                cudaStream_t st) {
+    if (prec == HAMR_FP64)
+        k_check_finite<double><<<nblk(NS, 256), 256, 0, st>>>((const double *)S, NS, gcode, ctl);
+    else
+        k_check_finite<float><<<nblk(NS, 256), 256, 0, st>>>((const float *)S, NS, gcode, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_state(int prec, const void *src, void *dst, long long NS, cudaStream_t st) {
+    const size_t bytes = (size_t)3 * NS * (prec == HAMR_FP64 ? 8 : 4);
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace hamr

@@ -1,0 +1,305 @@
+"""Python binding of the C ABI in include/hamr.h (argument marshalling only).
+
+Every step of the stochastic-LLG Heun path runs in the CUDA library libhamr.so; this
+module only converts arguments.  There is no CPU fallback: importing works without the
+library, but the first call raises if libhamr.so has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import GAMMA
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhamr.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NUMERIC, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
+LATTICE = {"sc": 0, "l10": 1}
+PRECISION = {"fp32": 0, "fp64": 1}
+NEIGHBOURS = {"stencil": 0, "csr": 1}
+EXPORTS = [
+    "hamr_lattice_create", "hamr_set_neighbour_shells", "hamr_set_csr", "hamr_set_grain_map",
+    "hamr_set_temperature_profile", "hamr_set_field_sequence", "hamr_set_moments",
+    "hamr_set_moments_device", "hamr_sllg_heun_steps", "hamr_sllg_heun_steps_async",
+    "hamr_synchronize", "hamr_read_moments", "hamr_read_moments_device",
+    "hamr_read_magnetisation", "hamr_clear_records", "hamr_read_energy", "hamr_get_step",
+    "hamr_set_step", "hamr_check_finite", "hamr_save_state", "hamr_load_state", "hamr_set_tile",
+    "hamr_get_tile", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
+]
+
+
+class HamrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hamr error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("precision", ctypes.c_int32), ("neighbours", ctypes.c_int32),
+        ("n_replicas", ctypes.c_int32),
+        ("dims", ctypes.POINTER(ctypes.c_int32)), ("seeds", ctypes.POINTER(ctypes.c_uint64)),
+        ("a", ctypes.c_double), ("c", ctypes.c_double),
+        ("periodic", ctypes.c_int32 * 3),
+        ("mu_s", ctypes.c_double), ("ku", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("dt", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libhamr.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhamr.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_2502_02236_gb300.build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "hamr_lattice_create": [vp, vp],
+            "hamr_set_neighbour_shells": [vp, i32, vp],
+            "hamr_set_csr": [vp, i32, vp, vp, vp],
+            "hamr_set_grain_map": [vp, i32, vp, i32],
+            "hamr_set_temperature_profile": [vp, i32, d, d, d, d, d, d, d],
+            "hamr_set_field_sequence": [vp, i32, d, vp, vp, i32, d, d, d, d],
+            "hamr_set_moments": [vp, i32, vp],
+            "hamr_set_moments_device": [vp, i32, vp],
+            "hamr_sllg_heun_steps": [vp, i64, i32],
+            "hamr_sllg_heun_steps_async": [vp, i64, i32],
+            "hamr_synchronize": [vp],
+            "hamr_read_moments": [vp, i32, vp],
+            "hamr_read_moments_device": [vp, i32, vp],
+            "hamr_read_magnetisation": [vp, i32, vp, i64, vp, vp, vp],
+            "hamr_clear_records": [vp],
+            "hamr_read_energy": [vp, i32, vp],
+            "hamr_get_step": [vp, vp],
+            "hamr_set_step": [vp, i64],
+            "hamr_check_finite": [vp],
+            "hamr_save_state": [vp, ctypes.c_char_p],
+            "hamr_load_state": [vp, ctypes.c_char_p],
+            "hamr_set_tile": [vp, i32, i32],
+            "hamr_get_tile": [vp, vp, vp],
+            "hamr_autotune": [vp, i32],
+            "hamr_query": [vp, i32, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.hamr_last_error.argtypes = [vp]
+        L.hamr_last_error.restype = ctypes.c_char_p
+        L.hamr_destroy.argtypes = [vp]
+        L.hamr_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _torch_current():
+    """(device ordinal, stream handle) of torch's current CUDA stream, or (0, None).  The
+    legacy default stream (handle 0) cannot be graph-captured: the library then makes its
+    own stream, and device-pointer calls must be ordered by the caller."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            s = torch.cuda.current_stream()
+            return torch.cuda.current_device(), (s.cuda_stream or None)
+    except Exception:
+        pass
+    return 0, None
+
+
+class Lattice:
+    """One hamr_t handle: n_replicas independent lattices advanced together."""
+
+    def __init__(self, dims, seeds, *, lattice="sc", precision="fp32", neighbours="stencil",
+                 a=0.25e-9, c=0.0, periodic=(False, False, False), mu_s, ku=0.0, alpha=0.1,
+                 dt=1e-16, gamma=GAMMA, device=None, stream="torch"):
+        L = lib()
+        self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+        self.R = self.dims.shape[0]
+        self.seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(-1))
+        if self.seeds.size != self.R:
+            raise ValueError("one seed per replica")
+        self.precision = precision
+        d = Desc()
+        d.lattice = LATTICE[lattice]
+        d.precision = PRECISION[precision]
+        d.neighbours = NEIGHBOURS[neighbours]
+        d.n_replicas = self.R
+        d.dims = self.dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.seeds = self.seeds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        d.a, d.c = a, c
+        for k in range(3):
+            d.periodic[k] = int(bool(periodic[k]))
+        d.mu_s, d.ku, d.alpha, d.dt, d.gamma = mu_s, ku, alpha, dt, gamma
+        tdev, tstream = _torch_current()
+        d.device = tdev if device is None else device
+        self.stream = tstream if stream == "torch" else stream
+        d.stream = self.stream
+        h = ctypes.c_void_p()
+        rc = L.hamr_lattice_create(ctypes.byref(h), ctypes.byref(d))
+        if rc != OK:
+            raise HamrError(rc, L.hamr_last_error(None).decode())
+        self._h = h
+
+    # -------------------------------------------------------------------- plumbing
+    def _ck(self, rc):
+        if rc != OK:
+            raise HamrError(rc, lib().hamr_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hamr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def n_sites(self, r):
+        nx, ny, nz = self.dims[r]
+        return int(nx) * int(ny) * int(nz)
+
+    # -------------------------------------------------------------------- setters
+    def set_neighbour_shells(self, J):
+        J = np.ascontiguousarray(np.asarray(J, dtype=np.float64).reshape(-1))
+        self._ck(lib().hamr_set_neighbour_shells(self._h, J.size, _p(J)))
+
+    def set_csr(self, replica, row_ptr, col, shell):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        sh = np.ascontiguousarray(shell, dtype=np.uint8)
+        self._ck(lib().hamr_set_csr(self._h, replica, _p(rp), _p(cl), _p(sh)))
+
+    def set_grain_map(self, replica, grain, n_grains):
+        g = np.ascontiguousarray(np.asarray(grain, dtype=np.int32).reshape(-1))
+        if g.size != self.n_sites(replica):
+            raise ValueError("grain map size %d != %d sites" % (g.size, self.n_sites(replica)))
+        self._ck(lib().hamr_set_grain_map(self._h, replica, _p(g), int(n_grains)))
+
+    def set_temperature_profile(self, replica, T_amb, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0):
+        self._ck(lib().hamr_set_temperature_profile(self._h, replica, T_amb, T_peak, fwhm, x0, y0, vx, vy))
+
+    def set_field_sequence(self, replica, B0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0,
+                           ramp_len=0.0, head_x0=0.0, head_v=0.0):
+        dr = np.ascontiguousarray(np.asarray(direction, dtype=np.float64))
+        b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1))
+        bp = _p(b) if b.size else None
+        self._ck(lib().hamr_set_field_sequence(self._h, replica, B0, _p(dr), bp, b.size, bit_len,
+                                               ramp_len, head_x0, head_v))
+
+    def set_moments(self, replica, S):
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+        if S.size != 3 * self.n_sites(replica):
+            raise ValueError("spin array must hold 3 x %d values" % self.n_sites(replica))
+        self._ck(lib().hamr_set_moments(self._h, replica, _p(S)))
+
+    def set_moments_device(self, replica, S):
+        """S: a contiguous float64 CUDA tensor of shape (n, 3) on the handle's device."""
+        if S.dtype != __import__("torch").float64 or not S.is_cuda or not S.is_contiguous():
+            raise ValueError("need a contiguous float64 CUDA tensor")
+        if S.numel() != 3 * self.n_sites(replica):
+            raise ValueError("spin tensor must hold 3 x %d values" % self.n_sites(replica))
+        self._ck(lib().hamr_set_moments_device(self._h, replica, ctypes.c_void_p(S.data_ptr())))
+
+    # -------------------------------------------------------------------- stepping
+    def sllg_heun_steps(self, n_steps, record_every=0):
+        self._ck(lib().hamr_sllg_heun_steps(self._h, int(n_steps), int(record_every)))
+
+    def sllg_heun_steps_async(self, n_steps, record_every=0):
+        self._ck(lib().hamr_sllg_heun_steps_async(self._h, int(n_steps), int(record_every)))
+
+    def synchronize(self):
+        self._ck(lib().hamr_synchronize(self._h))
+
+    # -------------------------------------------------------------------- readers
+    def read_moments(self, replica, out=None):
+        n = self.n_sites(replica)
+        if out is None:
+            out = np.empty((n, 3))
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 3 * n
+        self._ck(lib().hamr_read_moments(self._h, replica, _p(out)))
+        return out
+
+    def read_moments_device(self, replica, out):
+        if out.numel() != 3 * self.n_sites(replica) or not out.is_contiguous():
+            raise ValueError("need a contiguous float64 CUDA tensor of 3 x n values")
+        self._ck(lib().hamr_read_moments_device(self._h, replica, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def read_magnetisation(self, replica, n_grains=0):
+        """(M_t [n_rec, 3], steps [n_rec], M_grain [n_grains, 3] or None)."""
+        n = ctypes.c_int64()
+        self._ck(lib().hamr_read_magnetisation(self._h, replica, None, 0, ctypes.byref(n), None, None))
+        M = np.zeros((max(n.value, 1), 3))
+        st = np.zeros(max(n.value, 1), dtype=np.int64)
+        G = np.zeros((max(n_grains, 1), 3)) if n_grains > 0 else None
+        self._ck(lib().hamr_read_magnetisation(self._h, replica, _p(M), n.value, ctypes.byref(n),
+                                               _p(G) if G is not None else None, _p(st)))
+        return M[:n.value], st[:n.value], (G[:n_grains] if G is not None else None)
+
+    def clear_records(self):
+        self._ck(lib().hamr_clear_records(self._h))
+
+    def read_energy(self, replica):
+        E = ctypes.c_double()
+        self._ck(lib().hamr_read_energy(self._h, replica, ctypes.byref(E)))
+        return E.value
+
+    @property
+    def step(self):
+        s = ctypes.c_int64()
+        self._ck(lib().hamr_get_step(self._h, ctypes.byref(s)))
+        return s.value
+
+    @step.setter
+    def step(self, value):
+        self._ck(lib().hamr_set_step(self._h, int(value)))
+
+    def check_finite(self):
+        rc = lib().hamr_check_finite(self._h)
+        if rc == ERR_NUMERIC:
+            return False
+        self._ck(rc)
+        return True
+
+    def save_state(self, path):
+        self._ck(lib().hamr_save_state(self._h, os.fsencode(path)))
+
+    def load_state(self, path):
+        self._ck(lib().hamr_load_state(self._h, os.fsencode(path)))
+
+    def set_tile(self, tx, ty):
+        self._ck(lib().hamr_set_tile(self._h, tx, ty))
+
+    def get_tile(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        self._ck(lib().hamr_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, steps_per_trial=20):
+        self._ck(lib().hamr_autotune(self._h, int(steps_per_trial)))
+        return self.get_tile()
+
+    def query(self, key):
+        v = ctypes.c_int64()
+        self._ck(lib().hamr_query(self._h, int(key), ctypes.byref(v)))
+        return v.value

@@ -1,0 +1,330 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 path 1e-9 on every spin component (spins are unit vectors, so this is
+relative); FP32 path 2e-4 on every spin component over up to 1000 steps.  Both hold at
+T = 0 and at T > 0 because the thermal field is drawn from the same Philox stream on both
+sides; only rounding differs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from common import gpu_lattice, initial, max_abs, oracle_for, oracle_params
+from paper_2502_02236_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOL32 = 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2502_02236_gb300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def run_both(w, n_steps, S0=None, precision=None, neighbours=None, record_every=0, tile=None):
+    """Advance GPU and oracle by n_steps from the same state; returns per-replica
+    (gpu spins, oracle spins, gpu records, oracle records)."""
+    R = len(w["replicas"])
+    S0 = S0 if S0 is not None else [initial(rep) for rep in w["replicas"]]
+    lat = gpu_lattice(w, precision=precision, neighbours=neighbours, S0=S0)
+    if tile:
+        lat.set_tile(*tile)
+    lat.sllg_heun_steps(n_steps, record_every)
+    out = []
+    for r in range(R):
+        o = oracle_for(w, r)
+        S = np.ascontiguousarray(S0[r], dtype=np.float64).copy()
+        Mo = o.run(S, 0, n_steps, record_every)
+        Mg, steps, _ = lat.read_magnetisation(r)
+        out.append((lat.read_moments(r), S, Mg, Mo))
+    lat.close()
+    return out
+
+
+def tiny_track(nx=45, ny=37, nz=9, seed=5, T=True, field=True, grains=True, a=0.25e-9):
+    """A granular SC piece with a fast laser and a fast head so that both drivers change
+    within a few hundred steps."""
+    g2 = I.voronoi_grains(nx, ny, a, a, 3e-9, 0.5e-9, seed) if grains else np.zeros((ny, nx), np.int32)
+    rep = dict(dims=(nx, ny, nz), seed=1000 + seed, grain=I.columnar(g2, nz), n_grains=int(g2.max()) + 1,
+               init="tilt")
+    if T:
+        rep["T"] = dict(T_amb=300.0, T_peak=900.0, fwhm=6e-9, x0=2e-9, y0=nx * a / 3, vx=2e4, vy=1e3)
+    if field:
+        rep["field"] = dict(B0=2.0, direction=(0.1, 0.0, 1.0), bits=I.bits_of("0110100"), bit_len=0.3e-9,
+                            ramp_len=0.05e-9, head_x0=-0.2e-9, head_v=2e4)
+    return rep
+
+
+def workload_of(reps, precision="fp32", **over):
+    w = dict(lattice="sc", precision=precision, neighbours="stencil", a=0.25e-9, c=0.0,
+             periodic=(False, False, False), mu_s=I.MU_S, ku=I.KU_SC, alpha=0.1, dt=1e-16, J=[I.J_SC],
+             replicas=reps)
+    w.update(over)
+    return w
+
+
+# --------------------------------------------------------------------------- FP64 plain path
+def test_fp64_sc32_pbc_T0_tilt():
+    w = I.workload("sc32_pbc")
+    w["replicas"][0]["T"] = dict(T_amb=0.0)
+    S0 = [I.initial_state(32 * 32 * 8, "tilt", seed=2, tilt_deg=30)]
+    (g, o, Mg, Mo), = run_both(w, 200, S0=S0, record_every=10)
+    assert max_abs(g, o) < TOL64
+    assert Mg.shape == Mo.shape == (20, 3)
+    assert max_abs(Mg, Mo) < TOL64
+
+
+def test_fp64_sc32_pbc_workload():
+    """The plain FP64 workload as specified: 32x32x8, 300 K, 1 T along -z, +z start, 2000
+    steps, M every 10 steps."""
+    w = I.workload("sc32_pbc")
+    (g, o, Mg, Mo), = run_both(w, 2000, record_every=10)
+    assert max_abs(g, o) < TOL64
+    assert Mg.shape == (200, 3)
+    assert max_abs(Mg, Mo) < TOL64
+
+
+def test_fp64_granular_drivers():
+    w = workload_of([tiny_track()], precision="fp64")
+    (g, o, Mg, Mo), = run_both(w, 400, record_every=50)
+    assert max_abs(g, o) < TOL64
+    assert max_abs(Mg, Mo) < TOL64
+
+
+# --------------------------------------------------------------------------- FP32 fused path
+def test_fp32_sc32_pbc_T0_tilt_1000():
+    w = I.workload("sc32_pbc", precision="fp32")
+    w["replicas"][0]["T"] = dict(T_amb=0.0)
+    S0 = [I.initial_state(32 * 32 * 8, "tilt", seed=2, tilt_deg=30)]
+    (g, o, Mg, Mo), = run_both(w, 1000, S0=S0, record_every=100)
+    assert max_abs(g, o) < TOL32
+    assert max_abs(Mg, Mo) < TOL32
+
+
+def test_fp32_sc32_pbc_thermal_1000():
+    w = I.workload("sc32_pbc", precision="fp32")
+    (g, o, Mg, Mo), = run_both(w, 1000, record_every=10)
+    assert max_abs(g, o) < TOL32
+    assert max_abs(Mg, Mo) < TOL32
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 8), (64, 16), (16, 16)])
+def test_fp32_granular_drivers_every_tile(tile):
+    w = workload_of([tiny_track()])
+    (g, o, Mg, Mo), = run_both(w, 500, record_every=100, tile=tile)
+    assert max_abs(g, o) < TOL32
+    assert max_abs(Mg, Mo) < TOL32
+
+
+def uneven_replicas():
+    """Uneven batch: a single spin, thin slabs, a ragged granular piece, a replica with no
+    magnetic site, and one with adjacent different grains (bonds that must be cut)."""
+    reps = [
+        dict(dims=(1, 1, 1), seed=11, init="tilt", T=dict(T_amb=500.0), field=dict(B0=1.0, direction=(0, 0, -1))),
+        dict(dims=(3, 70, 5), seed=12, init="random", T=dict(T_amb=700.0)),
+        dict(dims=(33, 2, 17), seed=13, init="tilt", T=dict(T_amb=100.0), field=dict(B0=0.5, direction=(1, 0, 0))),
+        tiny_track(40, 29, 8, seed=7),
+        dict(dims=(5, 4, 3), seed=15, grain=np.full(60, -1, np.int32), n_grains=0, init="+z"),
+    ]
+    g = np.zeros((9, 10), np.int32)
+    g[:, 5:] = 1
+    reps.append(dict(dims=(10, 9, 4), seed=16, grain=I.columnar(g, 4), n_grains=2, init="random",
+                     T=dict(T_amb=400.0)))
+    return reps
+
+
+def test_fp32_batched_uneven():
+    w = workload_of(uneven_replicas())
+    for r, (g, o, Mg, Mo) in enumerate(run_both(w, 300, record_every=30)):
+        assert max_abs(g, o) < TOL32, r
+        assert max_abs(Mg, Mo) < TOL32, r
+
+
+def test_fp64_batched_uneven():
+    w = workload_of(uneven_replicas(), precision="fp64")
+    for r, (g, o, Mg, Mo) in enumerate(run_both(w, 300, record_every=30)):
+        assert max_abs(g, o) < TOL64, r
+        assert max_abs(Mg, Mo) < TOL64, r
+
+
+def test_periodic_tiny_lattices_both_precisions():
+    """Periodic lattices smaller than a tile, down to 1 x 1 x 1 (a site is its own neighbour)."""
+    reps = [dict(dims=d, seed=20 + k, init="random", T=dict(T_amb=300.0), field=dict(B0=1.0, direction=(0, 0, 1)))
+            for k, d in enumerate([(1, 1, 1), (2, 2, 2), (3, 1, 2), (2, 5, 1), (7, 3, 3)])]
+    for prec, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        w = workload_of(reps, precision=prec, periodic=(True, True, True))
+        for r, (g, o, Mg, Mo) in enumerate(run_both(w, 200, record_every=20)):
+            assert max_abs(g, o) < tol, (prec, r)
+
+
+# --------------------------------------------------------------------------- neighbour lists
+def l10_piece(nx=24, ny=20, nz=6, seed=3):
+    la, lc = 0.385e-9, 0.371e-9
+    ap = la / np.sqrt(2)
+    g2 = I.voronoi_grains(nx, ny, ap, ap, 3e-9, 0.5e-9, seed)
+    rep = dict(dims=(nx, ny, nz), seed=300 + seed, grain=I.columnar(g2, nz), n_grains=int(g2.max()) + 1,
+               init="tilt", T=dict(T_amb=400.0, T_peak=800.0, fwhm=4e-9, x0=3e-9, y0=3e-9, vx=1e4),
+               field=dict(B0=1.0, direction=(0, 0, -1)))
+    return dict(lattice="l10", precision="fp64", neighbours="csr", a=la, c=lc, periodic=(False, True, False),
+                mu_s=I.MU_S, ku=I.KU_L10, alpha=0.1, dt=1e-16, J=[I.J_SC, 0.5 * I.J_SC, 0.1 * I.J_SC],
+                replicas=[rep])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_l10_three_shells(prec, tol):
+    w = l10_piece()
+    (g, o, Mg, Mo), = run_both(w, 300, precision=prec, record_every=50)
+    assert max_abs(g, o) < tol
+    assert max_abs(Mg, Mo) < tol
+
+
+def test_sc_list_matches_stencil():
+    w = workload_of([tiny_track(31, 22, 7, seed=9)], precision="fp64", periodic=(True, False, True))
+    (gs, o, _, _), = run_both(w, 100)
+    (gc, _, _, _), = run_both(w, 100, neighbours="csr")
+    assert max_abs(gs, gc) < 1e-12
+    assert max_abs(gc, o) < TOL64
+
+
+def test_external_list_same_as_built():
+    """A list given through hamr_set_csr (here the geometric bond list) gives the same
+    trajectory as the list the library builds."""
+    w = l10_piece(12, 10, 4)
+    rep = w["replicas"][0]
+    o = oracle_for(w, 0)
+    rp, col, sh = o.neighbours()
+    S0 = [initial(rep)]
+    ref = gpu_lattice(w, S0=S0)
+    ref.sllg_heun_steps(100)
+    lat = gpu_lattice(w, S0=S0)
+    lat.set_csr(0, rp.astype(np.int32), col.astype(np.int32), sh.astype(np.uint8))
+    lat.set_moments(0, S0[0])
+    lat.sllg_heun_steps(100)
+    assert max_abs(lat.read_moments(0), ref.read_moments(0)) < 1e-12
+
+
+# --------------------------------------------------------------------------- reductions, energy
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_grain_averages_and_energy(prec, tol):
+    rep = tiny_track(48, 40, 6, seed=4)
+    w = workload_of([rep], precision=prec)
+    S0 = [initial(rep)]
+    lat = gpu_lattice(w, S0=S0)
+    lat.sllg_heun_steps(120, 40)
+    o = oracle_for(w, 0)
+    S = S0[0].copy()
+    o.run(S, 0, 120)
+    M, steps, Mg = lat.read_magnetisation(0, rep["n_grains"])
+    assert list(steps) == [40, 80, 120]
+    sums, counts = o.grain_sums(S, rep["n_grains"])
+    want = np.where(counts[:, None] > 0, sums / np.maximum(counts[:, None], 1), 0.0)
+    assert max_abs(Mg, want) < tol
+    assert max_abs(M[-1], o.magnetisation(S)) < tol
+    E = lat.read_energy(0)
+    Eo = o.energy(S, 120)
+    assert abs(E - Eo) <= (1e-9 if prec == "fp64" else 2e-4) * abs(Eo)
+
+
+# --------------------------------------------------------------------------- state handling
+def test_checkpoint_resume_bitwise(tmp_path):
+    w = workload_of(uneven_replicas()[:4])
+    lat = gpu_lattice(w)
+    lat.sllg_heun_steps(60, 20)
+    path = str(tmp_path / "state.bin")
+    lat.save_state(path)
+    lat.sllg_heun_steps(45, 0)
+    want = [lat.read_moments(r) for r in range(4)]
+    assert lat.step == 105
+    other = gpu_lattice(w)
+    other.load_state(path)
+    assert other.step == 60
+    other.sllg_heun_steps(20, 0)
+    other.sllg_heun_steps(25, 7)       # split differently, with records on the way
+    for r in range(4):
+        assert np.array_equal(other.read_moments(r), want[r])
+
+
+def test_autotune_keeps_state():
+    w = workload_of(uneven_replicas())
+    lat = gpu_lattice(w)
+    lat.sllg_heun_steps(10)
+    before = [lat.read_moments(r) for r in range(len(w["replicas"]))]
+    tile = lat.autotune(3)
+    assert lat.step == 10
+    assert tile in [(32, 8), (32, 16), (64, 8), (64, 16), (16, 16)]
+    for r, b in enumerate(before):
+        assert np.array_equal(lat.read_moments(r), b)
+
+
+def test_finite_check_flags_injected_nan():
+    w = workload_of([dict(dims=(8, 8, 4), seed=1, init="+z")])
+    lat = gpu_lattice(w)
+    assert lat.check_finite()
+    S = initial(w["replicas"][0])
+    S[17, 1] = np.nan
+    lat.set_moments(0, S)
+    assert not lat.check_finite()
+
+
+def test_device_pointer_roundtrip():
+    import torch
+    w = workload_of([tiny_track(20, 18, 5, seed=8)], precision="fp64")
+    rep = w["replicas"][0]
+    lat = gpu_lattice(w)
+    S0 = initial(rep, "random", seed=3)
+    t = torch.from_numpy(S0).cuda()
+    lat.set_moments_device(0, t)
+    out = torch.empty_like(t)
+    lat.read_moments_device(0, out)
+    torch.cuda.synchronize()
+    want = I.mask_void(S0, rep["grain"])
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+# --------------------------------------------------------------------------- full sizes, sampled
+def sample_sites(w, r, k, seed):
+    rep = w["replicas"][r]
+    n = int(np.prod(rep["dims"]))
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = rep["dims"]
+    edges = [0, nx - 1, nx * (ny - 1), n - 1, n // 2]
+    return np.unique(np.concatenate([rng.integers(0, n, size=k), edges]))
+
+
+@pytest.mark.parametrize("name", ["sc_track", "l10_window"])
+def test_full_size_one_step_sampled(name):
+    """One step of the full-size workload, compared at sampled sites that the oracle
+    computes one by one from the same pre-step state."""
+    w = I.workload(name)
+    S0 = [initial(rep) for rep in w["replicas"]]
+    lat = gpu_lattice(w, S0=S0)
+    lat.sllg_heun_steps(1, 1)
+    g = lat.read_moments(0)
+    sites = sample_sites(w, 0, 3000, 1)
+    want = orc.step_sites(oracle_params(w, 0), w["replicas"][0]["grain"], S0[0], 0, sites)
+    assert max_abs(g[sites], want) < TOL32
+    assert np.abs(g[sites] - S0[0][sites]).max() > 1e-3     # the step did move the spins
+
+
+def test_full_size_ensemble_sampled():
+    """The batched 256-replica workload in its benchmark launch configuration: one step,
+    sampled sites of every replica against the oracle."""
+    w = I.workload("ensemble256")
+    S0 = [initial(rep) for rep in w["replicas"]]
+    lat = gpu_lattice(w, S0=S0)
+    lat.autotune(2)
+    lat.sllg_heun_steps(1, 1)
+    worst = 0.0
+    for r in range(len(w["replicas"])):
+        sites = sample_sites(w, r, 40, r)
+        want = orc.step_sites(oracle_params(w, r), w["replicas"][r]["grain"], S0[r], 0, sites)
+        worst = max(worst, max_abs(lat.read_moments(r)[sites], want))
+    assert worst < TOL32
