@@ -211,6 +211,42 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial);
  * 3 = kernel launches per step (excluding records), 4 = storage slots. */
 int hamr_query(hamr_t h, int32_t key, int64_t *value);
 
+/* ---- One step without allocation ------------------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot allocate device
+ * memory themselves (code running while another framework owns the whole device memory
+ * pool, or a host loop that must not allocate after start-up) and so cannot create a
+ * hamr_t.  It advances one simple-cubic lattice (implicit 6-neighbour stencil, one exchange
+ * energy J) by one FP64 Heun step, with the same arithmetic and the same Philox stream as
+ * the FP64 path of hamr_sllg_heun_steps, a static applied field B_app and the laser spot of
+ * hamr_set_temperature_profile.
+ *   S_in, S_out: caller-owned device arrays of 3 n doubles (site-major, x fastest); they
+ *                may be the same array.  Non-magnetic sites are copied unchanged.
+ *   grain:       caller-owned device array of n int32 grain ids (-1 = non-magnetic), or
+ *                NULL for one grain.
+ *   step:        the n of t_n = n dt (thermal-field counter and laser position).
+ *   stream:      cudaStream_t; the call only enqueues two kernels and returns.
+ * Intermediate results live in one fixed device array (9 doubles per site, for at most
+ * HAMR_NOALLOC_MAX_SITES sites, about 9.4 MB) that every GPU loading the library holds until
+ * the process exits.  No call allocates or frees memory.  The first call on a device looks
+ * up that array's address (cudaGetSymbolAddress) and should come before any stream capture.
+ * All calls share the array and it keeps the last call's contents (nothing in it needs to
+ * start at zero): calls that overlap on the GPU race.  Errors (hamr_last_error(NULL) holds
+ * the message): ARG (null pointer, bad parameter, more than HAMR_NOALLOC_MAX_SITES sites),
+ * CUDA. */
+#define HAMR_NOALLOC_MAX_SITES 131072
+
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t periodic[3];
+    double a, mu_s, J, ku, alpha, dt, gamma;   /* as in hamr_lattice_desc; J of the one shell */
+    uint64_t seed;                             /* Philox key */
+    double T_amb, T_peak, fwhm, x0, y0, vx, vy; /* as in hamr_set_temperature_profile */
+    double B_app[3];                           /* static applied field [T] */
+} hamr_noalloc_params;
+
+int hamr_sllg_heun_step_noalloc(const hamr_noalloc_params *p, const double *S_in, double *S_out,
+                                const int32_t *grain, int64_t step, void *stream);
+
 /* Message of the last failed call on this handle (never NULL). */
 const char *hamr_last_error(hamr_t h);
 

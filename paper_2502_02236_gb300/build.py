@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhamr.so")
-SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused.cu", "kernels_misc.cu"]
+SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused.cu", "kernels_misc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

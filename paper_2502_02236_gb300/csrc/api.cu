@@ -538,6 +538,11 @@ int init_device(hamr_t h, long long NS, long long maxn, const std::vector<int> &
 }  // namespace
 
 // =====================================================================================
+namespace hamr {
+// error message of a call that has no handle (read back with hamr_last_error(NULL))
+void set_handleless_error(const char *msg) { g_create_err = msg; }
+}  // namespace hamr
+
 extern "C" {
 
 int hamr_lattice_create(hamr_t *out, const hamr_lattice_desc *d) {

@@ -26,7 +26,9 @@ EXPORTS = [
     "hamr_read_magnetisation", "hamr_clear_records", "hamr_read_energy", "hamr_get_step",
     "hamr_set_step", "hamr_check_finite", "hamr_save_state", "hamr_load_state", "hamr_set_tile",
     "hamr_get_tile", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
+    "hamr_sllg_heun_step_noalloc",
 ]
+NOALLOC_MAX_SITES = 131072
 
 
 class HamrError(RuntimeError):
@@ -45,6 +47,19 @@ class Desc(ctypes.Structure):
         ("mu_s", ctypes.c_double), ("ku", ctypes.c_double), ("alpha", ctypes.c_double),
         ("dt", ctypes.c_double), ("gamma", ctypes.c_double),
         ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+class NoallocParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("periodic", ctypes.c_int32 * 3),
+        ("a", ctypes.c_double), ("mu_s", ctypes.c_double), ("J", ctypes.c_double),
+        ("ku", ctypes.c_double), ("alpha", ctypes.c_double), ("dt", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("T_amb", ctypes.c_double), ("T_peak", ctypes.c_double), ("fwhm", ctypes.c_double),
+        ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("vx", ctypes.c_double),
+        ("vy", ctypes.c_double), ("B_app", ctypes.c_double * 3),
     ]
 
 
@@ -86,6 +101,7 @@ def lib():
             "hamr_get_tile": [vp, vp, vp],
             "hamr_autotune": [vp, i32],
             "hamr_query": [vp, i32, vp],
+            "hamr_sllg_heun_step_noalloc": [vp, vp, vp, vp, i64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -303,3 +319,26 @@ class Lattice:
         v = ctypes.c_int64()
         self._ck(lib().hamr_query(self._h, int(key), ctypes.byref(v)))
         return v.value
+
+
+def sllg_heun_step_noalloc(dims, S_in, S_out, *, grain=None, step=0, periodic=(False, False, False),
+                           a, mu_s, J, ku=0.0, alpha=0.1, dt=1e-16, gamma=GAMMA, seed=0, T_amb=0.0,
+                           T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0, B_app=(0.0, 0.0, 0.0),
+                           stream=None):
+    """One FP64 Heun step through hamr_sllg_heun_step_noalloc on caller-owned device
+    tensors: S_in, S_out float64 (n, 3) (may be the same tensor), grain int32 (n,) or None.
+    The library allocates nothing; the call is stream-ordered on `stream` (a raw handle,
+    None = the legacy default stream)."""
+    p = NoallocParams()
+    p.nx, p.ny, p.nz = (int(v) for v in dims)
+    for k in range(3):
+        p.periodic[k] = int(bool(periodic[k]))
+        p.B_app[k] = float(B_app[k])
+    p.a, p.mu_s, p.J, p.ku, p.alpha, p.dt, p.gamma = a, mu_s, J, ku, alpha, dt, gamma
+    p.seed = int(seed)
+    p.T_amb, p.T_peak, p.fwhm, p.x0, p.y0, p.vx, p.vy = T_amb, T_peak, fwhm, x0, y0, vx, vy
+    g = ctypes.c_void_p(grain.data_ptr()) if grain is not None else None
+    rc = lib().hamr_sllg_heun_step_noalloc(ctypes.byref(p), ctypes.c_void_p(S_in.data_ptr()),
+                                           ctypes.c_void_p(S_out.data_ptr()), g, int(step), stream)
+    if rc != OK:
+        raise HamrError(rc, lib().hamr_last_error(None).decode())
