@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--tile", default=None, help="fused-kernel shape THREADSxSTAGED instead of autotuning")
     return p.parse_args()
 
 
@@ -265,7 +266,11 @@ def main():
                 else int(np.prod(rep["dims"])) for rep in w["replicas"])
 
     lat = build_lattice(w, "fp32", dist.rank)
-    tile = lat.autotune(5)
+    if args.tile:
+        lat.set_tile(*(int(v) for v in args.tile.split("x")))
+        tile = lat.get_tile()
+    else:
+        tile = lat.autotune(5)
     lat.sllg_heun_steps(W - W % rec + rec, rec)
     prime(lat, K, rec)
     prime(lat, K, 0)

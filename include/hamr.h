@@ -199,12 +199,15 @@ int hamr_check_finite(hamr_t h);
 int hamr_save_state(hamr_t h, const char *path);
 int hamr_load_state(hamr_t h, const char *path);
 
-/* Tile shape of the fused FP32 stencil kernel: threads tx * ty cover a (tx-2) x (ty-2)
- * block of columns plus a one-site halo.  hamr_autotune times the compiled shapes on the
- * current state (advancing nothing: state and step are restored) and keeps the fastest.
- * hamr_get_tile reports the shape in use.  Errors: ARG (shape not compiled), CUDA. */
-int hamr_set_tile(hamr_t h, int32_t tx, int32_t ty);
-int hamr_get_tile(hamr_t h, int32_t *tx, int32_t *ty);
+/* Launch shape of the fused FP32 stencil kernel: CTA size `threads` and `staged`, the number
+ * of positions per plane a CTA stages in shared memory.  Each replica is split into column
+ * blocks whose staged region, the block plus a two-column halo, fits `staged`; the split is
+ * chosen per replica by a work model.  Compiled pairs: (1024, 1536), (512, 768), (1024, 1280),
+ * (256, 768).  hamr_autotune times every compiled pair on the current state (advancing
+ * nothing: state and step are restored) and keeps the fastest.  Errors: ARG (pair not
+ * compiled), STATE, CUDA. */
+int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged);
+int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged);
 int hamr_autotune(hamr_t h, int32_t steps_per_trial);
 
 /* Sizes: key 0 = total lattice sites, 1 = magnetic sites, 2 = device bytes held,

@@ -224,16 +224,19 @@ int refresh_grains(hamr_t h) {
         std::copy(h->gcount_rep[r].begin(), h->gcount_rep[r].end(), h->gcount_h.begin() + h->reps_h[r].grain_off);
     if (G > h->G_cap) {
         dfree(h->grain_acc_d);
+        dfree(h->grain_fx_d);
         dfree(h->grain_last_d);
         dfree(h->gcount_d);
         const int cap = std::max(G, 2 * h->G_cap);
         CK(h, dalloc(h, &h->grain_acc_d, 3 * (size_t)cap));
+        CK(h, dalloc(h, &h->grain_fx_d, 3 * (size_t)cap));
         CK(h, dalloc(h, &h->grain_last_d, 3 * (size_t)cap));
         CK(h, dalloc(h, &h->gcount_d, (size_t)cap));
         h->G_cap = cap;
         clear_graphs(h);
     }
     CK(h, cudaMemsetAsync(h->grain_acc_d, 0, sizeof(double) * 3 * h->G_cap, h->stream));
+    CK(h, cudaMemsetAsync(h->grain_fx_d, 0, sizeof(unsigned long long) * 3 * h->G_cap, h->stream));
     CK(h, cudaMemsetAsync(h->grain_last_d, 0, sizeof(double) * 3 * h->G_cap, h->stream));
     CK(h, cudaMemcpyAsync(h->gcount_d, h->gcount_h.data(), sizeof(long long) * G, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->nmag_d, h->nmag_h.data(), sizeof(long long) * h->R, cudaMemcpyHostToDevice, h->stream));
@@ -244,44 +247,112 @@ int refresh_grains(hamr_t h) {
 }
 
 // ---------------------------------------------------------------- fused work list
-// Split each replica into column blocks of at most (tx-2) x (ty-2), balanced in size, and
-// order the blocks by decreasing cost so that the persistent CTAs finish together.
+// Split of one replica into ntx x nty balanced column blocks for a kernel variant.  Among the
+// splits whose staged region fits the variant, the one with the least modelled work per
+// plane wins: predictor on every listed column (interior plus the halo inside the lattice),
+// corrector on the interior, staging of the region, and a fixed cost per block.
+void choose_split(const ReplicaDev &R, const int per[3], const FusedVariant &v, int &bx_out, int &by_out) {
+    double best = 1e300;
+    bx_out = by_out = 1;
+    for (int ntx = 1; ntx <= R.nx; ++ntx) {
+        const int bx = (R.nx + ntx - 1) / ntx;
+        if (ntx > 1 && bx == (R.nx + ntx - 2) / (ntx - 1)) continue;  // same width as ntx - 1
+        const int tx = (R.nx + bx - 1) / bx;
+        if ((bx + 4) * 5 > v.staged) continue;
+        for (int nty = 1; nty <= R.ny; ++nty) {
+            const int by = (R.ny + nty - 1) / nty;
+            if (nty > 1 && by == (R.ny + nty - 2) / (nty - 1)) continue;
+            const int ty = (R.ny + by - 1) / by;
+            if ((bx + 4) * (by + 4) > v.staged || (bx + 2) * (by + 2) > v.threads * v.per_thread) continue;
+            const double A = (double)(R.nx + 2 * tx - (per[0] ? 0 : 2)) * (R.ny + 2 * ty - (per[1] ? 0 : 2));
+            const double I = (double)R.nx * R.ny;
+            const double S = (double)tx * ty * (bx + 4) * (by + 4);
+            const double cost = 2.0 * A + I + 0.3 * S + 0.06 * v.threads * tx * ty;
+            if (cost < best) {
+                best = cost;
+                bx_out = bx;
+                by_out = by;
+            }
+        }
+    }
+}
+
+// Work items and their column lists for the current variant.  A column is listed when it
+// lies inside the lattice (or wraps on a periodic axis) and holds a magnetic site on some
+// plane; interior columns come first.  Items are ordered by decreasing cost so that the
+// persistent CTAs finish together.
 int build_items(hamr_t h) {
-    const int bxm = h->tile_tx - 2, bym = h->tile_ty - 2;
+    FusedVariant v;
+    if (!fused_variant(h->variant, v)) return fail(h, HAMR_ERR_ARG, "unknown kernel variant %d", h->variant);
     std::vector<WorkItem> items;
     std::vector<long long> cost;
+    std::vector<std::vector<uint16_t>> lists;
     for (int r = 0; r < h->R; ++r) {
         const ReplicaDev &R = h->reps_h[r];
-        const int nbx = (R.nx + bxm - 1) / bxm, nby = (R.ny + bym - 1) / bym;
-        const int bx = (R.nx + nbx - 1) / nbx, by = (R.ny + nby - 1) / nby;
-        for (int j = 0; j < nby; ++j)
-            for (int i = 0; i < nbx; ++i) {
+        // columns holding a magnetic site on some plane
+        std::vector<uint8_t> col(R.nx * (size_t)R.ny, 0);
+        for (long long z = 0; z < R.nz; ++z)
+            for (long long y = 0; y < R.ny; ++y)
+                for (long long x = 0; x < R.nx; ++x)
+                    if (h->gcode_h[slot_of(R, x, y, z)]) col[x + (size_t)R.nx * y] = 1;
+        int BX, BY;
+        choose_split(R, h->per, v, BX, BY);
+        for (int y0 = 0; y0 < R.ny; y0 += BY)
+            for (int x0 = 0; x0 < R.nx; x0 += BX) {
+                const int bx = std::min(BX, R.nx - x0), by = std::min(BY, R.ny - y0);
+                const int WS = bx + 4;
+                std::vector<uint16_t> inner, halo;
+                for (int sy = 1; sy <= by + 2; ++sy)
+                    for (int sx = 1; sx <= bx + 2; ++sx) {
+                        int cx = x0 - 2 + sx, cy = y0 - 2 + sy;
+                        if (!wrap(cx, R.nx, h->per[0]) || !wrap(cy, R.ny, h->per[1])) continue;
+                        if (!col[cx + (size_t)R.nx * cy]) continue;
+                        const bool in = sx >= 2 && sx <= bx + 1 && sy >= 2 && sy <= by + 1;
+                        (in ? inner : halo).push_back((uint16_t)(sx + WS * sy));
+                    }
+                if (inner.empty()) continue;  // nothing to update in this block
                 WorkItem w;
                 w.r = r;
-                w.x0 = i * bx;
-                w.y0 = j * by;
-                const int wx = std::min(bx, R.nx - w.x0), wy = std::min(by, R.ny - w.y0);
-                if (wx <= 0 || wy <= 0) continue;
-                w.bxy = wx | (wy << 16);
+                w.x0 = x0;
+                w.y0 = y0;
+                w.bxy = bx | (by << 16);
+                w.list_off = 0;
+                w.counts = (int)(inner.size() + halo.size()) | ((int)inner.size() << 16);
+                inner.insert(inner.end(), halo.begin(), halo.end());
                 items.push_back(w);
-                cost.push_back((long long)(wx + 2) * (wy + 2) * (R.nz + 2));
+                lists.push_back(std::move(inner));
+                cost.push_back((long long)(2 * (w.counts & 0xffff) + (w.counts >> 16) + 64) * (R.nz + 2));
             }
     }
     std::vector<size_t> idx(items.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
     std::vector<WorkItem> sorted(items.size());
-    for (size_t i = 0; i < idx.size(); ++i) sorted[i] = items[idx[i]];
-    if ((int)sorted.size() > h->items_cap) {
+    std::vector<uint16_t> flat;
+    for (size_t i = 0; i < idx.size(); ++i) {
+        sorted[i] = items[idx[i]];
+        sorted[i].list_off = (int)flat.size();
+        flat.insert(flat.end(), lists[idx[i]].begin(), lists[idx[i]].end());
+    }
+    if (sorted.size() > (size_t)h->items_cap) {
         dfree(h->items_d);
         CK(h, dalloc(h, &h->items_d, sorted.size()));
         h->items_cap = (int)sorted.size();
     }
-    CK(h, cudaMemcpyAsync(h->items_d, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice,
-                          h->stream));
+    if (flat.size() > h->lists_cap) {
+        dfree(h->lists_d);
+        CK(h, dalloc(h, &h->lists_d, flat.size()));
+        h->lists_cap = flat.size();
+    }
+    if (!sorted.empty())
+        CK(h, cudaMemcpyAsync(h->items_d, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice,
+                              h->stream));
+    if (!flat.empty())
+        CK(h, cudaMemcpyAsync(h->lists_d, flat.data(), sizeof(uint16_t) * flat.size(), cudaMemcpyHostToDevice,
+                              h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->n_items = (int)sorted.size();
-    const int bps = std::max(1, fused_max_blocks_per_sm(h->tile_tx, h->tile_ty));
+    const int bps = std::max(1, fused_max_blocks_per_sm(h->variant));
     h->fused_grid = std::max(1, std::min(h->n_items, bps * h->num_sms));
     h->items_dirty = false;
     clear_graphs(h);
@@ -298,6 +369,7 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.reps = h->reps_d;
         a.bits = h->bits_d;
         a.items = h->items_d;
+        a.lists = h->lists_d;
         a.n_items = h->n_items;
         a.ctl = h->ctl_d;
         a.cJ = (float)h->ph.cJ[0];
@@ -310,12 +382,12 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.ay = (float)h->ph.ay;
         a.az = (float)h->ph.az;
         for (int d = 0; d < 3; ++d) a.per[d] = h->per[d];
-        a.grain_acc = h->grain_acc_d;
+        a.grain_fx = h->grain_fx_d;
         a.Sbuf0 = (float *)h->S[0];
         a.Sbuf1 = (float *)h->S[1];
         for (int i = 0; i < G; ++i) {
             a.step_off = i;
-            CK(h, launch_fused_step(h->tile_tx, h->tile_ty, a, h->fused_grid, record && i == G - 1, h->stream));
+            CK(h, launch_fused_step(h->variant, a, h->fused_grid, record && i == G - 1, h->stream));
         }
     } else {
         const int nb = (int)(h->NS / PLAIN_BLOCK);
@@ -362,12 +434,12 @@ int enqueue_block(hamr_t h, int G, bool record) {
         }
     }
     CK(h, launch_bookkeeping(h->ctl_d, G, record, h->R, h->reps_d, h->nmag_d, h->gcount_d, h->G, h->grain_acc_d,
-                             h->grain_last_d, h->rec_d, h->rec_cap, h->rec_step_d, h->stream));
+                             h->grain_fx_d, h->grain_last_d, h->rec_d, h->rec_cap, h->rec_step_d, h->stream));
     return HAMR_OK;
 }
 
 int run_block(hamr_t h, int G, bool record) {
-    const auto key = std::make_tuple(G, record ? 1 : 0, 0, h->tile_tx * 1000 + h->tile_ty);
+    const auto key = std::make_tuple(G, record ? 1 : 0, 0, h->variant);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t graph;
@@ -483,9 +555,11 @@ void destroy_device(hamr_t h) {
     dfree(h->bits_d);
     dfree(h->ctl_d);
     dfree(h->grain_acc_d);
+    dfree(h->grain_fx_d);
     dfree(h->grain_last_d);
     dfree(h->gcount_d);
     dfree(h->nmag_d);
+    dfree(h->lists_d);
     dfree(h->rec_d);
     dfree(h->rec_step_d);
     dfree(h->dscratch_d);
@@ -660,9 +734,8 @@ int hamr_lattice_create(hamr_t *out, const hamr_lattice_desc *d) {
         if (h->own_stream) cudaStreamDestroy(h->stream);
         return rc;
     }
-    // default tile shape; hamr_autotune picks the fastest compiled one
-    h->tile_tx = 32;
-    h->tile_ty = 8;
+    // default kernel variant; hamr_autotune picks the fastest compiled one
+    h->variant = 0;
     *out = hp.release();
     return HAMR_OK;
 }
@@ -1038,22 +1111,34 @@ int hamr_load_state(hamr_t h, const char *path) {
     return hamr_set_step(h, step);
 }
 
-int hamr_set_tile(hamr_t h, int32_t tx, int32_t ty) {
+static int find_variant(int threads, int staged) {
+    FusedVariant v;
+    for (int i = 0; fused_variant(i, v); ++i)
+        if (v.threads == threads && v.staged == staged) return i;
+    return -1;
+}
+
+int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged) {
     if (!h) return HAMR_ERR_ARG;
-    if (!fused_shape_compiled(tx, ty)) return fail(h, HAMR_ERR_ARG, "tile %d x %d is not compiled", tx, ty);
+    const int v = find_variant(threads, staged);
+    if (v < 0) return fail(h, HAMR_ERR_ARG, "no compiled kernel variant with %d threads, %d staged positions", threads,
+                           staged);
     DeviceGuard dg(h->device);
-    if (fused_max_blocks_per_sm(tx, ty) < 1) return fail(h, HAMR_ERR_ARG, "tile %d x %d cannot launch", tx, ty);
-    h->tile_tx = tx;
-    h->tile_ty = ty;
-    h->items_dirty = true;
-    clear_graphs(h);
+    if (fused_max_blocks_per_sm(v) < 1) return fail(h, HAMR_ERR_ARG, "variant %d cannot launch", v);
+    if (v != h->variant) {
+        h->variant = v;
+        h->items_dirty = true;
+        clear_graphs(h);
+    }
     return HAMR_OK;
 }
 
-int hamr_get_tile(hamr_t h, int32_t *tx, int32_t *ty) {
-    if (!h || !tx || !ty) return HAMR_ERR_ARG;
-    *tx = h->tile_tx;
-    *ty = h->tile_ty;
+int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged) {
+    if (!h || !threads || !staged) return HAMR_ERR_ARG;
+    FusedVariant v;
+    fused_variant(h->variant, v);
+    *threads = v.threads;
+    *staged = v.staged;
     return HAMR_OK;
 }
 
@@ -1069,17 +1154,16 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     CK(h, launch_copy_state(h->prec, h->S[h->cur], backup, h->NS, h->stream));
     const long long step0 = h->step_h;
     const int cur0 = h->cur;
-    std::vector<std::pair<int, int>> shapes;
-    fused_shapes(shapes);
     float best = 1e30f;
-    int btx = h->tile_tx, bty = h->tile_ty;
+    int bestv = h->variant;
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     int rc = HAMR_OK;
-    for (auto &s : shapes) {
-        if (fused_max_blocks_per_sm(s.first, s.second) < 1) continue;
-        if ((rc = hamr_set_tile(h, s.first, s.second))) break;
+    FusedVariant v;
+    for (int i = 0; fused_variant(i, v); ++i) {
+        if (fused_max_blocks_per_sm(i) < 1) continue;
+        if ((rc = hamr_set_tile(h, v.threads, v.staged))) break;
         if ((rc = steps_impl(h, steps_per_trial, 0, true))) break;  // warm-up, graph capture
         CK(h, cudaEventRecord(e0, h->stream));
         if ((rc = steps_impl(h, steps_per_trial, 0, false))) break;
@@ -1089,8 +1173,7 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
         CK(h, cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
-            btx = s.first;
-            bty = s.second;
+            bestv = i;
         }
     }
     cudaEventDestroy(e0);
@@ -1102,7 +1185,8 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     int rc2 = hamr_set_step(h, step0);
     if (rc) return rc;
     if (rc2) return rc2;
-    return hamr_set_tile(h, btx, bty);
+    fused_variant(bestv, v);
+    return hamr_set_tile(h, v.threads, v.staged);
 }
 
 int hamr_query(hamr_t h, int32_t key, int64_t *value) {

@@ -13,23 +13,41 @@ namespace hamr {
 // SC'11): per round, 32x32->64-bit products of counter words 0 and 2 with 0xD2511F53 and
 // 0xCD9E8D57; the new words are (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key advances
 // by (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox_round(uint4 c, unsigned k0, unsigned k1) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    return make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k0, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ k1, (unsigned)p0);
+}
+
 __device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = philox_round(c, k0, k1);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
     return c;
 }
 
+// The same generator with the ten round keys precomputed: rk[r] = (k0_r, k1_r, k0_r+1, k1_r+1)
+// for r = 0, 2, 4, 6, 8 (kept in shared memory by the fused kernel and read by broadcast).
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint4 *rk) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const uint4 k = rk[r];
+        c = philox_round(c, k.x, k.y);
+        c = philox_round(c, k.z, k.w);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_ctr(unsigned long long site, unsigned long long step) {
+    return make_uint4((unsigned)site, (unsigned)(site >> 32), (unsigned)step, (unsigned)(step >> 32));
+}
+
 __device__ __forceinline__ uint4 philox_site(unsigned k0, unsigned k1, unsigned long long site,
                                              unsigned long long step) {
-    return philox10(make_uint4((unsigned)site, (unsigned)(site >> 32), (unsigned)step,
-                               (unsigned)(step >> 32)),
-                    k0, k1);
+    return philox10(philox_ctr(site, step), k0, k1);
 }
 
 // Box-Muller on u_k = (x_k + 1/2) 2^-32: (r1 cos 2pi u1, r1 sin 2pi u1, r2 cos 2pi u3),
@@ -46,16 +64,24 @@ __device__ __forceinline__ void normals3(uint4 x, double &n0, double &n1, double
     n2 = r2 * cospi(2.0 * u3);
 }
 
+// The FP32 path evaluates the same formulas in FP32 with the hardware approximations:
+// u_k = x_k 2^-32 + 2^-33 (one rounding), -2 ln u = -2 ln2 log2(u) kept above 1e-30 so
+// that u rounded up to 1 gives a radius of ~0 rather than a NaN, sqrt(t) = t rsqrt(t), and
+// the angles centred on (-pi, pi) where the sine and cosine approximations are accurate:
+// cos 2pi u = -cos(2pi (u - 1/2)), sin 2pi u = -sin(2pi (u - 1/2)).
 __device__ __forceinline__ void normals3(uint4 x, float &n0, float &n1, float &n2) {
-    const float s = 2.3283064365386963e-10f;  // 2^-32
-    const float u0 = fmaf((float)x.x, s, 0.5f * s), u1 = fmaf((float)x.y, s, 0.5f * s);
-    const float u2 = fmaf((float)x.z, s, 0.5f * s), u3 = fmaf((float)x.w, s, 0.5f * s);
-    const float r1 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+    const float s = 2.3283064365386963e-10f, h = 1.1641532182693481e-10f;  // 2^-32, 2^-33
+    const float u0 = fmaf((float)x.x, s, h), u1 = fmaf((float)x.y, s, h);
+    const float u2 = fmaf((float)x.z, s, h), u3 = fmaf((float)x.w, s, h);
+    const float m2ln2 = -1.3862943611198906f;  // -2 ln 2
+    const float t1 = fmaxf(m2ln2 * __log2f(u0), 1e-30f), t2 = fmaxf(m2ln2 * __log2f(u2), 1e-30f);
+    const float r1 = t1 * rsqrtf(t1), r2 = t2 * rsqrtf(t2);
+    const float twopi = 6.2831853071795865f;
     float sn, cs;
-    sincospif(2.0f * u1, &sn, &cs);
-    n0 = r1 * cs;
-    n1 = r1 * sn;
-    n2 = r2 * cospif(2.0f * u3);
+    __sincosf(twopi * (u1 - 0.5f), &sn, &cs);
+    n0 = -r1 * cs;
+    n1 = -r1 * sn;
+    n2 = -r2 * __cosf(twopi * (u3 - 0.5f));
 }
 
 // Write-field polarity s(t): linear ramp from bit b-1 to bit b over the first ramp_len of
@@ -128,6 +154,37 @@ __device__ __forceinline__ void grain_accumulate(double *acc, int g, double sx, 
         atomicAdd(acc + 3 * key + 0, sx);
         atomicAdd(acc + 3 * key + 1, sy);
         atomicAdd(acc + 3 * key + 2, sz);
+    }
+}
+
+// Exact magnetisation sums of the FP32 path: each spin component is rounded to a multiple
+// of 2^-24 (FP32 resolution at 1) and summed as 64-bit integers, so the sum does not depend
+// on the order in which CTAs add it.  The warp adds lanes that share a grain by shuffles,
+// then one 64-bit atomic per component.
+constexpr float FX_SCALE = 16777216.0f;  // 2^24
+
+__device__ __forceinline__ void grain_accumulate_fx(unsigned long long *acc, int g, long long sx, long long sy,
+                                                    long long sz, bool active) {
+    const unsigned full = 0xffffffffu;
+    const int key = active ? g : -1;
+    const int k0 = __shfl_sync(full, key, 0);
+    if (__all_sync(full, key == k0)) {
+        if (k0 < 0) return;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(full, sx, o);
+            sy += __shfl_xor_sync(full, sy, o);
+            sz += __shfl_xor_sync(full, sz, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(acc + 3 * k0 + 0, (unsigned long long)sx);
+            atomicAdd(acc + 3 * k0 + 1, (unsigned long long)sy);
+            atomicAdd(acc + 3 * k0 + 2, (unsigned long long)sz);
+        }
+    } else if (key >= 0) {
+        atomicAdd(acc + 3 * key + 0, (unsigned long long)sx);
+        atomicAdd(acc + 3 * key + 1, (unsigned long long)sy);
+        atomicAdd(acc + 3 * key + 2, (unsigned long long)sz);
     }
 }
 

@@ -63,9 +63,18 @@ struct Ctl {
 
 // One unit of work of the fused kernel: a block of columns of one replica.
 struct WorkItem {
-    int r;        // replica
-    int x0, y0;   // first interior column
-    int bxy;      // interior width | height << 16
+    int r;         // replica
+    int x0, y0;    // first interior column
+    int bxy;       // interior width | height << 16
+    int list_off;  // first entry of its column list
+    int counts;    // listed columns | interior columns << 16
+};
+
+// A compiled variant of the fused kernel.
+struct FusedVariant {
+    int threads;     // CTA size
+    int per_thread;  // list entries per thread (listed columns <= threads * per_thread)
+    int staged;      // staged positions per plane ((bx + 4) * (by + 4) <= staged)
 };
 
 template <typename Real>
@@ -91,23 +100,23 @@ struct FusedArgs {
     const ReplicaDev *reps;
     const uint8_t *bits;
     const WorkItem *items;
+    const uint16_t *lists;      // column lists of all items (staged-region positions)
     int n_items;
     Ctl *ctl;
     int step_off;
     float cJ, cK, pref, alpha, dt, sig0, ax, ay, az;
     int per[3];
-    double *grain_acc;
+    unsigned long long *grain_fx;  // [G][3] fixed-point (2^-24) sums at record steps
 };
 
 // kernel launchers (kernels_*.cu)
 cudaError_t launch_plain_step(int prec, const void *args, int n_blocks, bool record, cudaStream_t st);
-cudaError_t launch_fused_step(int tx, int ty, const FusedArgs &a, int grid, bool record, cudaStream_t st);
-bool fused_shape_compiled(int tx, int ty);
-int fused_max_blocks_per_sm(int tx, int ty);
-void fused_shapes(std::vector<std::pair<int, int>> &out);
+cudaError_t launch_fused_step(int variant, const FusedArgs &a, int grid, bool record, cudaStream_t st);
+bool fused_variant(int variant, FusedVariant &out);
+int fused_max_blocks_per_sm(int variant);
 cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps,
                                const long long *nmag, const long long *gcount, int Gtot, double *grain_acc,
-                               double *grain_last, double *rec, long long rec_cap,
+                               unsigned long long *grain_fx, double *grain_last, double *rec, long long rec_cap,
                                long long *rec_step, cudaStream_t st);
 cudaError_t launch_init_state(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
 cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
@@ -165,6 +174,7 @@ struct hamr_ctx {
     std::vector<int> n_grains;        // per replica
     int G = 0, G_cap = 0;             // total grain bins and allocated capacity
     double *grain_acc_d = nullptr, *grain_last_d = nullptr;
+    unsigned long long *grain_fx_d = nullptr;
     long long *gcount_d = nullptr, *nmag_d = nullptr;
     std::vector<long long> gcount_h, nmag_h;
     std::vector<std::vector<long long>> gcount_rep;   // per replica, per grain
@@ -181,9 +191,11 @@ struct hamr_ctx {
     long long step_h = 0;             // host mirror of the step counter
 
     // fused kernel tiling
-    int tile_tx = 32, tile_ty = 8;
+    int variant = 0;
     hamr::WorkItem *items_d = nullptr;
     int n_items = 0, items_cap = 0;
+    uint16_t *lists_d = nullptr;
+    size_t lists_cap = 0;
     int fused_grid = 0;
     bool items_dirty = true;
     int num_sms = 0;

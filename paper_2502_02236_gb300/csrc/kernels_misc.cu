@@ -9,10 +9,16 @@ namespace hamr {
 // per-grain FP64 sums into the replica magnetisation M = sum S / N_mag (Eq. 6 as an
 // average over magnetic sites), per-grain averages, and clear the sums.
 __global__ void k_bookkeeping(Ctl *ctl, int G, int record, int R, const ReplicaDev *reps, const long long *nmag,
-                              const long long *gcount, int Gtot, double *grain_acc, double *grain_last,
-                              double *rec, long long rec_cap, long long *rec_step) {
+                              const long long *gcount, int Gtot, double *grain_acc, unsigned long long *grain_fx,
+                              double *grain_last, double *rec, long long rec_cap, long long *rec_step) {
     const long long after = ctl->step + G;
     if (record) {
+        // fold the FP32 path's exact fixed-point sums (units of 2^-24) into the FP64 sums
+        for (int g = threadIdx.x; g < 3 * Gtot; g += blockDim.x) {
+            grain_acc[g] += (double)(long long)grain_fx[g] * 5.9604644775390625e-08;
+            grain_fx[g] = 0ull;
+        }
+        __syncthreads();
         const long long idx = ctl->n_rec;
         for (int r = threadIdx.x; r < R; r += blockDim.x) {
             const int g0 = reps[r].grain_off, ng = reps[r].n_grains;
@@ -48,10 +54,11 @@ __global__ void k_bookkeeping(Ctl *ctl, int G, int record, int R, const ReplicaD
 }
 
 cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps, const long long *nmag,
-                               const long long *gcount, int Gtot, double *grain_acc, double *grain_last,
-                               double *rec, long long rec_cap, long long *rec_step, cudaStream_t st) {
-    k_bookkeeping<<<1, 256, 0, st>>>(ctl, G, record ? 1 : 0, R, reps, nmag, gcount, Gtot, grain_acc, grain_last,
-                                     rec, rec_cap, rec_step);
+                               const long long *gcount, int Gtot, double *grain_acc, unsigned long long *grain_fx,
+                               double *grain_last, double *rec, long long rec_cap, long long *rec_step,
+                               cudaStream_t st) {
+    k_bookkeeping<<<1, 256, 0, st>>>(ctl, G, record ? 1 : 0, R, reps, nmag, gcount, Gtot, grain_acc, grain_fx,
+                                     grain_last, rec, rec_cap, rec_step);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,10 @@ def test_fp32_sc32_pbc_thermal_1000():
     assert max_abs(Mg, Mo) < TOL32
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 8), (64, 16), (16, 16)])
+TILES = [(1024, 1536), (512, 768), (1024, 1280), (256, 768)]
+
+
+@pytest.mark.parametrize("tile", TILES)
 def test_fp32_granular_drivers_every_tile(tile):
     w = workload_of([tiny_track()])
     (g, o, Mg, Mo), = run_both(w, 500, record_every=100, tile=tile)
@@ -153,6 +156,35 @@ def test_fp64_batched_uneven():
     for r, (g, o, Mg, Mo) in enumerate(run_both(w, 300, record_every=30)):
         assert max_abs(g, o) < TOL64, r
         assert max_abs(Mg, Mo) < TOL64, r
+
+
+@pytest.mark.parametrize("periodic", [(False, False, False), (True, True, False), (True, False, True)])
+def test_fp32_multi_tile_splits(periodic):
+    """Replicas wider than one column block in x and y, open and periodic, so that halos
+    between blocks and across periodic edges are exercised."""
+    reps = [tiny_track(150, 140, 6, seed=31), tiny_track(70, 66, 5, seed=32, grains=False),
+            dict(dims=(97, 3, 4), seed=33, init="random", T=dict(T_amb=600.0))]
+    w = workload_of(reps, periodic=periodic)
+    for r, (g, o, Mg, Mo) in enumerate(run_both(w, 120, record_every=40)):
+        assert max_abs(g, o) < TOL32, r
+        assert max_abs(Mg, Mo) < TOL32, r
+
+
+def test_fp32_non_columnar_grains():
+    """Grains that change along z, touching grains (bonds cut by the grain mask) and scattered
+    non-magnetic sites."""
+    nx, ny, nz = 37, 29, 11
+    x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    g = ((x // 9 + y // 7 + z // 3) % 4).transpose(2, 1, 0).reshape(-1).astype(np.int32)
+    rng = np.random.default_rng(5)
+    g[rng.uniform(size=g.size) < 0.1] = -1
+    rep = dict(dims=(nx, ny, nz), seed=41, grain=g, n_grains=4, init="random",
+               T=dict(T_amb=350.0, T_peak=700.0, fwhm=4e-9, x0=4e-9, y0=3e-9, vx=1e4))
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        w = workload_of([rep], precision=prec)
+        (gg, o, Mg, Mo), = run_both(w, 150, record_every=50)
+        assert max_abs(gg, o) < tol, prec
+        assert max_abs(Mg, Mo) < tol, prec
 
 
 def test_periodic_tiny_lattices_both_precisions():
@@ -259,7 +291,7 @@ def test_autotune_keeps_state():
     before = [lat.read_moments(r) for r in range(len(w["replicas"]))]
     tile = lat.autotune(3)
     assert lat.step == 10
-    assert tile in [(32, 8), (32, 16), (64, 8), (64, 16), (16, 16)]
+    assert tile in TILES
     for r, b in enumerate(before):
         assert np.array_equal(lat.read_moments(r), b)
 
