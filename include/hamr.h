@@ -200,12 +200,13 @@ int hamr_save_state(hamr_t h, const char *path);
 int hamr_load_state(hamr_t h, const char *path);
 
 /* Launch shape of the fused FP32 stencil kernel: CTA size `threads` and `staged`, the number
- * of positions per plane a CTA stages in shared memory.  Each replica is split into column
- * blocks whose staged region, the block plus a two-column halo, fits `staged`; the split is
- * chosen per replica by a work model.  Compiled pairs: (1024, 1536), (512, 768), (1024, 1280),
- * (256, 768).  hamr_autotune times every compiled pair on the current state (advancing
- * nothing: state and step are restored) and keeps the fastest.  Errors: ARG (pair not
- * compiled), STATE, CUDA. */
+ * of positions per plane a CTA stages in shared memory (row pitch x rows).  Each replica is
+ * split into column blocks that fit the shape: the block plus a two-column halo within the
+ * staged region, and the block plus a one-column halo within `threads`; the split is chosen
+ * per replica by a work model.  Compiled (threads, pitch x rows): (1024, 68 x 24),
+ * (512, 36 x 24), (256, 36 x 14), (1024, 36 x 40).  hamr_autotune times every compiled shape
+ * on the current state (advancing nothing: state and step are restored) and keeps the
+ * fastest.  Errors: ARG (shape not compiled), STATE, CUDA. */
 int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged);
 int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged);
 int hamr_autotune(hamr_t h, int32_t steps_per_trial);

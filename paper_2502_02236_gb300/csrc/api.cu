@@ -247,28 +247,88 @@ int refresh_grains(hamr_t h) {
 }
 
 // ---------------------------------------------------------------- fused work list
-// Split of one replica into ntx x nty balanced column blocks for a kernel variant.  Among the
-// splits whose staged region fits the variant, the one with the least modelled work per
-// plane wins: predictor on every listed column (interior plus the halo inside the lattice),
-// corrector on the interior, staging of the region, and a fixed cost per block.
-void choose_split(const ReplicaDev &R, const int per[3], const FusedVariant &v, int &bx_out, int &by_out) {
+// Listed columns of the block [x0, x0+bx) x [y0, y0+by) with its one-column halo: columns
+// inside the lattice (or wrapping on a periodic axis) that hold a magnetic site; pre is the
+// 2-D prefix sum of that column mask (halo columns that wrap are counted through the mask).
+struct ColumnMask {
+    int nx, ny, per_x, per_y;
+    std::vector<uint8_t> m;
+    std::vector<int> pre;  // (ny + 1) x (nx + 1)
+    int at(int x, int y) const {
+        if (!wrap(x, nx, per_x) || !wrap(y, ny, per_y)) return 0;
+        return m[x + (size_t)nx * y];
+    }
+    int rect(int x0, int x1, int y0, int y1) const {  // [x0, x1) x [y0, y1) inside the lattice
+        return pre[x1 + (nx + 1) * (size_t)y1] - pre[x0 + (nx + 1) * (size_t)y1] - pre[x1 + (nx + 1) * (size_t)y0] +
+               pre[x0 + (nx + 1) * (size_t)y0];
+    }
+    int listed(int x0, int y0, int bx, int by) const {
+        const int xa = std::max(x0 - 1, 0), xb = std::min(x0 + bx + 1, nx);
+        const int ya = std::max(y0 - 1, 0), yb = std::min(y0 + by + 1, ny);
+        int n = rect(xa, xb, ya, yb);
+        // halo columns beyond a periodic edge wrap to columns counted again
+        if (per_x || per_y) {
+            n = 0;
+            for (int y = y0 - 1; y <= y0 + by; ++y)
+                for (int x = x0 - 1; x <= x0 + bx; ++x) n += at(x, y);
+        }
+        return n;
+    }
+};
+
+ColumnMask column_mask(hamr_t h, int r) {
+    const ReplicaDev &R = h->reps_h[r];
+    ColumnMask c;
+    c.nx = R.nx;
+    c.ny = R.ny;
+    c.per_x = h->per[0];
+    c.per_y = h->per[1];
+    c.m.assign((size_t)R.nx * R.ny, 0);
+    for (long long z = 0; z < R.nz; ++z)
+        for (long long y = 0; y < R.ny; ++y)
+            for (long long x = 0; x < R.nx; ++x)
+                if (h->gcode_h[slot_of(R, x, y, z)]) c.m[x + (size_t)R.nx * y] = 1;
+    c.pre.assign((size_t)(R.nx + 1) * (R.ny + 1), 0);
+    for (int y = 0; y < R.ny; ++y)
+        for (int x = 0; x < R.nx; ++x)
+            c.pre[(x + 1) + (R.nx + 1) * (size_t)(y + 1)] = c.m[x + (size_t)R.nx * y] + c.pre[x + (R.nx + 1) * (size_t)(y + 1)] +
+                                                             c.pre[(x + 1) + (R.nx + 1) * (size_t)y] -
+                                                             c.pre[x + (R.nx + 1) * (size_t)y];
+    return c;
+}
+
+// Split of one replica into ntx x nty balanced column blocks for a kernel variant.  A split
+// fits when every block's staged region (block + two-column halo) fits the variant's pitch
+// and rows and every block lists at most one column per thread.  Among fitting splits the
+// one with the least modelled time wins: per block and plane, a fixed cost for the CTA's
+// threads, the predictor on the listed columns, the corrector on the interior and the
+// staging of the region.
+void choose_split(const ReplicaDev &R, const ColumnMask &cm, const FusedVariant &v, int margin, int &bx_out,
+                  int &by_out) {
     double best = 1e300;
     bx_out = by_out = 1;
     for (int ntx = 1; ntx <= R.nx; ++ntx) {
         const int bx = (R.nx + ntx - 1) / ntx;
         if (ntx > 1 && bx == (R.nx + ntx - 2) / (ntx - 1)) continue;  // same width as ntx - 1
-        const int tx = (R.nx + bx - 1) / bx;
-        if ((bx + 4) * 5 > v.staged) continue;
+        if (bx + margin > v.pitch) continue;
         for (int nty = 1; nty <= R.ny; ++nty) {
             const int by = (R.ny + nty - 1) / nty;
             if (nty > 1 && by == (R.ny + nty - 2) / (nty - 1)) continue;
-            const int ty = (R.ny + by - 1) / by;
-            if ((bx + 4) * (by + 4) > v.staged || (bx + 2) * (by + 2) > v.threads * v.per_thread) continue;
-            const double A = (double)(R.nx + 2 * tx - (per[0] ? 0 : 2)) * (R.ny + 2 * ty - (per[1] ? 0 : 2));
-            const double I = (double)R.nx * R.ny;
-            const double S = (double)tx * ty * (bx + 4) * (by + 4);
-            const double cost = 2.0 * A + I + 0.3 * S + 0.06 * v.threads * tx * ty;
-            if (cost < best) {
+            if (by + 4 > v.rows) continue;
+            double cost = 0.0;
+            bool fits = true;
+            for (int y0 = 0; y0 < R.ny && fits; y0 += by)
+                for (int x0 = 0; x0 < R.nx; x0 += bx) {
+                    const int wx = std::min(bx, R.nx - x0), wy = std::min(by, R.ny - y0);
+                    const int listed = cm.listed(x0, y0, wx, wy);
+                    if (listed > v.threads) {
+                        fits = false;
+                        break;
+                    }
+                    const int inner = cm.rect(x0, x0 + wx, y0, y0 + wy);
+                    cost += 0.25 * v.threads + 2.0 * listed + inner + 0.3 * (wx + 4) * (wy + 4);
+                }
+            if (fits && cost < best) {
                 best = cost;
                 bx_out = bx;
                 by_out = by;
@@ -277,30 +337,78 @@ void choose_split(const ReplicaDev &R, const int per[3], const FusedVariant &v, 
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, found at run time (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// Tensor maps of replica r's spin state in each buffer: a 4-D view (x over the storage pitch,
+// y, z, component) whose box is one staged plane of all three components.
+int build_maps(hamr_t h, int r, const FusedVariant &v, CUtensorMap out[2]) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(h, HAMR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const ReplicaDev &R = h->reps_h[r];
+    const cuuint64_t dim[4] = {(cuuint64_t)R.px, (cuuint64_t)R.ny, (cuuint64_t)R.nz, 3};
+    const cuuint64_t stride[3] = {(cuuint64_t)R.px * 4, (cuuint64_t)R.px * R.ny * 4, (cuuint64_t)h->NS * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)v.pitch, (cuuint32_t)v.rows, 1, 3};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        void *base = (float *)h->S[b] + R.off;
+        const CUresult e = enc(&out[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dim, stride, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (e != CUDA_SUCCESS)
+            return fail(h, HAMR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for replica %d", (int)e, r);
+    }
+    return HAMR_OK;
+}
+
 // Work items and their column lists for the current variant.  A column is listed when it
 // lies inside the lattice (or wraps on a periodic axis) and holds a magnetic site on some
-// plane; interior columns come first.  Items are ordered by decreasing cost so that the
-// persistent CTAs finish together.
+// plane; interior columns come first.
 int build_items(hamr_t h) {
     FusedVariant v;
     if (!fused_variant(h->variant, v)) return fail(h, HAMR_ERR_ARG, "unknown kernel variant %d", h->variant);
     std::vector<WorkItem> items;
     std::vector<long long> cost;
     std::vector<std::vector<uint16_t>> lists;
+    std::vector<CUtensorMap> maps(2 * (size_t)h->R);
+    memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    h->tma_ok.assign(h->R, 0);
     for (int r = 0; r < h->R; ++r) {
         const ReplicaDev &R = h->reps_h[r];
+        // TMA tiles cannot wrap: replicas with periodic x or y, or touching grains, are staged by
+        // per-position copies
+        const int tma = !h->per[0] && !h->per[1] && !R.cross_grain;
+        h->tma_ok[r] = tma;
+        if (tma) {
+            int rc = build_maps(h, r, v, &maps[2 * (size_t)r]);
+            if (rc) return rc;
+        }
         // columns holding a magnetic site on some plane
-        std::vector<uint8_t> col(R.nx * (size_t)R.ny, 0);
-        for (long long z = 0; z < R.nz; ++z)
-            for (long long y = 0; y < R.ny; ++y)
-                for (long long x = 0; x < R.nx; ++x)
-                    if (h->gcode_h[slot_of(R, x, y, z)]) col[x + (size_t)R.nx * y] = 1;
+        const ColumnMask cm = column_mask(h, r);
+        const std::vector<uint8_t> &col = cm.m;
         int BX, BY;
-        choose_split(R, h->per, v, BX, BY);
+        choose_split(R, cm, v, tma ? 7 : 4, BX, BY);
         for (int y0 = 0; y0 < R.ny; y0 += BY)
             for (int x0 = 0; x0 < R.nx; x0 += BX) {
                 const int bx = std::min(BX, R.nx - x0), by = std::min(BY, R.ny - y0);
-                const int WS = bx + 4;
+                const int WS = v.pitch;
+                // staged origin: x0 - 2, rounded down to a multiple of 4 columns for TMA
+                const int dx0 = tma ? (((x0 - 2) % 4) + 4) % 4 : 0;
                 std::vector<uint16_t> inner, halo;
                 for (int sy = 1; sy <= by + 2; ++sy)
                     for (int sx = 1; sx <= bx + 2; ++sx) {
@@ -308,7 +416,7 @@ int build_items(hamr_t h) {
                         if (!wrap(cx, R.nx, h->per[0]) || !wrap(cy, R.ny, h->per[1])) continue;
                         if (!col[cx + (size_t)R.nx * cy]) continue;
                         const bool in = sx >= 2 && sx <= bx + 1 && sy >= 2 && sy <= by + 1;
-                        (in ? inner : halo).push_back((uint16_t)(sx + WS * sy));
+                        (in ? inner : halo).push_back((uint16_t)(sx + dx0 + WS * sy));
                     }
                 if (inner.empty()) continue;  // nothing to update in this block
                 WorkItem w;
@@ -318,15 +426,28 @@ int build_items(hamr_t h) {
                 w.bxy = bx | (by << 16);
                 w.list_off = 0;
                 w.counts = (int)(inner.size() + halo.size()) | ((int)inner.size() << 16);
-                inner.insert(inner.end(), halo.begin(), halo.end());
+                w.stage = tma | (dx0 << 8);
+                // interior columns first, flagged by bit 15 (corrected by the thread that lists them)
+                std::vector<uint16_t> mixed;
+                mixed.reserve(inner.size() + halo.size());
+                for (uint16_t p : inner) mixed.push_back((uint16_t)(p | 0x8000u));
+                mixed.insert(mixed.end(), halo.begin(), halo.end());
                 items.push_back(w);
-                lists.push_back(std::move(inner));
+                lists.push_back(std::move(mixed));
                 cost.push_back((long long)(2 * (w.counts & 0xffff) + (w.counts >> 16) + 64) * (R.nz + 2));
             }
     }
+    // replicas by decreasing total cost, the blocks of a replica together and in row order:
+    // neighbouring blocks then run at the same time and share their halo planes through L2
+    std::vector<long long> rcost(h->R, 0);
+    for (size_t i = 0; i < items.size(); ++i) rcost[items[i].r] += cost[i];
     std::vector<size_t> idx(items.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        const int ra = items[a].r, rb = items[b].r;
+        if (ra != rb) return rcost[ra] != rcost[rb] ? rcost[ra] > rcost[rb] : ra < rb;
+        return a < b;
+    });
     std::vector<WorkItem> sorted(items.size());
     std::vector<uint16_t> flat;
     for (size_t i = 0; i < idx.size(); ++i) {
@@ -350,6 +471,9 @@ int build_items(hamr_t h) {
     if (!flat.empty())
         CK(h, cudaMemcpyAsync(h->lists_d, flat.data(), sizeof(uint16_t) * flat.size(), cudaMemcpyHostToDevice,
                               h->stream));
+    if (!h->maps_d) CK(h, dalloc(h, &h->maps_d, 2 * (size_t)h->R));
+    CK(h, cudaMemcpyAsync(h->maps_d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                          h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->n_items = (int)sorted.size();
     const int bps = std::max(1, fused_max_blocks_per_sm(h->variant));
@@ -383,6 +507,7 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.az = (float)h->ph.az;
         for (int d = 0; d < 3; ++d) a.per[d] = h->per[d];
         a.grain_fx = h->grain_fx_d;
+        a.maps = h->maps_d;
         a.Sbuf0 = (float *)h->S[0];
         a.Sbuf1 = (float *)h->S[1];
         for (int i = 0; i < G; ++i) {
@@ -467,6 +592,11 @@ int collect_records(hamr_t h) {
     CK(h, cudaStreamSynchronize(h->stream));
     Ctl c;
     CK(h, cudaMemcpy(&c, h->ctl_d, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.err & 2) {
+        const int zero = 0;
+        CK(h, cudaMemcpy(&h->ctl_d->err, &zero, sizeof zero, cudaMemcpyHostToDevice));
+        return fail(h, HAMR_ERR_TIMEOUT, "a bounded wait in the fused kernel ran out; the state is not valid");
+    }
     if (c.n_rec > 0) {
         const long long n = std::min(c.n_rec, h->rec_cap);
         const size_t old = h->rec_h.size();
@@ -534,10 +664,7 @@ int steps_impl(hamr_t h, int64_t n_steps, int32_t record_every, bool sync) {
         left -= G;
     }
     if (nrec > 0) h->pending_records = true;
-    if (sync) {
-        if (h->pending_records) return collect_records(h);
-        CK(h, cudaStreamSynchronize(h->stream));
-    }
+    if (sync) return collect_records(h);
     return HAMR_OK;
 }
 
@@ -560,6 +687,7 @@ void destroy_device(hamr_t h) {
     dfree(h->gcount_d);
     dfree(h->nmag_d);
     dfree(h->lists_d);
+    dfree(h->maps_d);
     dfree(h->rec_d);
     dfree(h->rec_step_d);
     dfree(h->dscratch_d);

@@ -2,6 +2,7 @@
 // constants, kernel argument blocks and the host context behind a hamr_t.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,7 +58,8 @@ struct Ctl {
     long long step;          // completed steps
     long long n_rec;         // records written since the host last collected them
     unsigned work_ctr[2];    // work-list counters of the persistent kernel (by step parity)
-    int err;                 // error flags (bit 0: bad value found by the finite check)
+    int err;                 // error flags (bit 0: bad value found by the finite check;
+                             // bit 1: a bounded wait of the fused kernel ran out)
     int pad_;
 };
 
@@ -68,13 +70,15 @@ struct WorkItem {
     int bxy;       // interior width | height << 16
     int list_off;  // first entry of its column list
     int counts;    // listed columns | interior columns << 16
+    int stage;     // 1: staged by TMA | columns between the staged origin and x0 - 2, << 8
 };
 
 // A compiled variant of the fused kernel.
 struct FusedVariant {
-    int threads;     // CTA size
-    int per_thread;  // list entries per thread (listed columns <= threads * per_thread)
-    int staged;      // staged positions per plane ((bx + 4) * (by + 4) <= staged)
+    int threads;  // CTA size; one listed column per thread
+    int pitch;    // staged-region row pitch: bx + 4 <= pitch
+    int rows;     // staged-region rows: by + 4 <= rows
+    int staged;   // pitch * rows
 };
 
 template <typename Real>
@@ -107,6 +111,7 @@ struct FusedArgs {
     float cJ, cK, pref, alpha, dt, sig0, ax, ay, az;
     int per[3];
     unsigned long long *grain_fx;  // [G][3] fixed-point (2^-24) sums at record steps
+    const CUtensorMap *maps;       // [R][2] tensor maps of each replica's state in each buffer
 };
 
 // kernel launchers (kernels_*.cu)
@@ -196,6 +201,8 @@ struct hamr_ctx {
     int n_items = 0, items_cap = 0;
     uint16_t *lists_d = nullptr;
     size_t lists_cap = 0;
+    CUtensorMap *maps_d = nullptr;    // [R][2] (variant-dependent box)
+    std::vector<int> tma_ok;          // replica staged by TMA (open in x and y, no grain mask)
     int fused_grid = 0;
     bool items_dirty = true;
     int num_sms = 0;

@@ -3,32 +3,55 @@
 //
 // Work item = a block of bx x by columns of one replica spanning all nz planes.  The CTA
 // stages, plane by plane, the spins of the block plus a two-column halo in shared memory and
-// marches up the planes.  At march step k it
-//   1. predicts S' on plane k for every listed column: the block's interior and its
+// marches up the planes.  Staging runs three planes ahead of the march through a four-slot
+// ring with one mbarrier per slot: one thread issues a TMA tile copy of the three spin
+// components (zero-filled beyond open edges); replicas whose blocks wrap around a periodic
+// edge, or whose grains touch, are staged instead by per-position cp.async copies that arrive
+// on the same mbarriers.  At march step k the CTA
+//   1. starts staging plane k+3 into the slot that plane k-1 has left;
+//   2. waits for plane k+1;
+//   3. predicts S' on plane k for every listed column: the block's interior and its
 //      one-column halo, so the corrector never needs another CTA's S';
-//   2. corrects plane k-1 on the interior columns from the S' planes k-2, k-1, k;
-//   3. stages plane k+2 (loads issued before step 1, stored to shared memory after step 2).
+//   4. synchronises once;
+//   5. corrects plane k-1 on the interior columns from the S' planes k-2, k-1, k.
+// With four S and four S' slots no other barrier is needed: the next step's writes go to
+// slots that no thread can still be reading.  The four slot mbarriers are initialised once
+// per kernel and keep running phases across work items.
 // The list of columns is built on the host per work item: only columns inside the lattice
-// that hold a magnetic site are listed (interior first), so lanes are not spent on the
-// non-magnetic grain boundaries or on halos beyond an open edge.  Each thread owns the same
-// P list entries for the whole march and keeps in registers what the next stage needs from
-// its own column: S and the grain code of the previous plane, dt f(S, B(S)) and the thermal
-// field of the plane awaiting correction.
+// that hold a magnetic site are listed, so lanes are not spent on the non-magnetic grain
+// boundaries or on halos beyond an open edge; interior columns come first, flagged in the
+// list entry.  Each thread owns one list
+// entry for the whole march and keeps in registers what the next stage needs from its own
+// column: S of the previous plane, dt f(S, B(S)) and the thermal field of the plane awaiting
+// correction.  The march is unrolled over the ring period so that ring slots and neighbour
+// offsets are compile-time constants.
 // Each site's thermal normals come from its own (replica key, site, step) Philox counter, so
 // halo sites computed by two CTAs get the same noise.  Open edges and non-magnetic sites read
-// as S = 0 (the state of such sites is kept at 0), so the exchange sum needs no mask unless
-// a replica has bonds between two different grains.
-// Per step the kernel reads S once (12 B/site) plus the 2-byte grain code and writes S once
-// (12 B/site); halo columns are re-read from L2.
+// as S = 0 (the state of such sites is kept at 0): a zero spin marks a non-magnetic site and
+// adds nothing to the exchange sum, so grain codes are read only at record steps (for the
+// per-grain sums) and for replicas whose grains touch (the exchange mask).
+// Per step the kernel reads S once (12 B/site) and writes S once (12 B/site); halo columns
+// are re-read from L2.
 #include "device_common.cuh"
 
 namespace hamr {
 
-template <int NT, int P, int CAPS>
+constexpr int NSLOT = 4;                  // ring depth (planes)
+constexpr unsigned WAIT_LIMIT = 1u << 22;  // polls of an mbarrier before the kernel gives up
+
+template <int NT, int SW, int SH>
 struct FusedShape {
-    static constexpr int LPT = (CAPS + NT - 1) / NT;  // staged positions per thread
-    // S planes k, k+1 | S' planes (3) | grain codes (4 planes)
-    static constexpr size_t smem = sizeof(float) * (2 * 3 * CAPS + 3 * 3 * CAPS) + sizeof(uint16_t) * 4 * CAPS;
+    static constexpr int CAPS = SW * SH;               // staged positions per plane
+    static constexpr int LPT = (CAPS + NT - 1) / NT;  // per-position copies per thread (fallback)
+    // one S slot: the TMA box [3 components][SH rows][SW columns], rounded to 128 B
+    static constexpr int SLOT_F = ((3 * CAPS * 4 + 127) / 128) * 128 / 4;
+    static constexpr size_t smem = 128 + sizeof(float) * NSLOT * SLOT_F + sizeof(float4) * NSLOT * CAPS +
+                                   sizeof(uint16_t) * NSLOT * CAPS;
+};
+
+template <int V>
+struct IC {
+    static constexpr int value = V;
 };
 
 __device__ __forceinline__ int wrap_coord(int v, int n, int per, bool &ok) {
@@ -40,16 +63,89 @@ __device__ __forceinline__ int wrap_coord(int v, int n, int per, bool &ok) {
     return ((v % n) + n) % n;
 }
 
-template <int NT, int P, int CAPS, bool RECORD>
+__device__ __forceinline__ bool nonzero3(float x, float y, float z) {
+    return ((__float_as_uint(x) | __float_as_uint(y) | __float_as_uint(z)) << 1) != 0u;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+
+// this thread's earlier cp.async copies arrive on b once they have landed
+__device__ __forceinline__ void mbar_arrive_cp_async(unsigned long long *b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false when the phase did not complete within WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+    for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+
+// TMA tile copy of box (x, y, z, component) of a 4-D tensor map into shared memory
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int c,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// dt f(S, B) for B = (J/mu_s) sum of the six neighbours (each weighted 0/1 when masked)
+//                    + (2 ku/mu_s) S_z z + B_app + B_th
+__device__ __forceinline__ void heun_rhs(const FusedArgs &a, float sx, float sy, float sz, float ex, float ey,
+                                         float ez, float bax, float bay, float baz, float tx, float ty, float tz,
+                                         float q, float &fx, float &fy, float &fz) {
+    const float bx = fmaf(a.cJ, ex, bax + tx);
+    const float by = fmaf(a.cJ, ey, bay + ty);
+    const float bz = fmaf(a.cJ, ez, fmaf(a.cK, sz, baz + tz));
+    const float cx = sy * bz - sz * by, cy = sz * bx - sx * bz, cz = sx * by - sy * bx;
+    const float sb = sx * bx + sy * by + sz * bz, ss = sx * sx + sy * sy + sz * sz;
+    fx = q * (cx + a.alpha * (sb * sx - ss * bx));
+    fy = q * (cy + a.alpha * (sb * sy - ss * by));
+    fz = q * (cz + a.alpha * (sb * sz - ss * bz));
+}
+
+template <int NT, int SW, int SH, bool RECORD>
 __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_fused(FusedArgs a) {
-    using Sh = FusedShape<NT, P, CAPS>;
-    constexpr int LPT = Sh::LPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *sS = reinterpret_cast<float *>(smem_raw);                 // [2][3][CAPS]
-    float *sP = sS + 2 * 3 * CAPS;                                    // [3][3][CAPS]
-    uint16_t *sG = reinterpret_cast<uint16_t *>(sP + 3 * 3 * CAPS);  // [4][CAPS]
+    using Sh = FusedShape<NT, SW, SH>;
+    constexpr int CAPS = Sh::CAPS, LPT = Sh::LPT, SLOT_F = Sh::SLOT_F;
+    extern __shared__ unsigned char smem_raw[];
+    float *sS = reinterpret_cast<float *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);  // [4][SLOT_F]
+    float4 *sP = reinterpret_cast<float4 *>(sS + NSLOT * SLOT_F);                          // [4][CAPS]
+    uint16_t *sG = reinterpret_cast<uint16_t *>(sP + NSLOT * CAPS);                        // [4][CAPS]
     __shared__ int s_item;
     __shared__ uint4 s_rk[5];  // Philox round keys of the current replica
+    __shared__ __align__(8) unsigned long long s_bar[NSLOT];
 
     const int tid = threadIdx.x;
     const long long NS = a.NS;
@@ -59,6 +155,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
     float *__restrict__ Sout = par ? a.Sbuf0 : a.Sbuf1;
     if (blockIdx.x == 0 && tid == 0) a.ctl->work_ctr[par ^ 1] = 0u;  // next step's counter
     const float t = (float)step * a.dt;
+    const float q = a.pref * a.dt;
+    bool stop = false;  // a bounded wait ran out (decided uniformly by barrier vote)
+    // The slot barriers live for the whole kernel: every thread arrives once per fill (the TMA
+    // issuer with the expected byte count, per-position copies through cp.async), and each
+    // thread tracks the parity of the next phase of every slot in ph.
+    unsigned ph = 0;
+    if (tid < NSLOT) mbar_init(&s_bar[tid], (unsigned)NT);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(&a.ctl->work_ctr[par], 1u);
@@ -68,300 +172,275 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
         const WorkItem W = a.items[it];
         const ReplicaDev &R = a.reps[W.r];
         const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px;
-        const long long off = R.off;
+        const int off = (int)R.off;
         const int plane = px * ny;
         const int bx = W.bxy & 0xffff, by = W.bxy >> 16;
-        const int WS = bx + 4, SA = WS * (by + 4);
-        const int n_act = W.counts & 0xffff, n_int = W.counts >> 16;
+        const int n_act = W.counts & 0xffff;
         const bool mask = R.cross_grain != 0;
+        const bool tma = (W.stage & 1) != 0;
+        const int xs = W.x0 - 2 - (W.stage >> 8), ys = W.y0 - 2;  // staged-region origin
+        const CUtensorMap *map = a.maps + 2 * W.r + par;
         if (tid < 5) {
             const unsigned k0 = R.key0 + 2u * tid * 0x9E3779B9u, k1 = R.key1 + 2u * tid * 0xBB67AE85u;
             s_rk[tid] = make_uint4(k0, k1, k0 + 0x9E3779B9u, k1 + 0xBB67AE85u);
         }
-        // S' of unlisted positions must read as 0 for the whole item
-        for (int i = tid; i < 9 * CAPS; i += NT) sP[i] = 0.0f;
+        // S' (and its grain code) of unlisted positions must read as 0 for the whole item
+        for (int i = tid; i < NSLOT * CAPS; i += NT) sP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
 
-        // this thread's list entries (site and storage indices fit in 32 bits: a replica
-        // has at most 2^30 sites and the storage fewer than 2^28 slots)
-        int pos[P];          // staged-region position, or -1
-        bool inner[P];       // interior column: corrected here
-        float sig[P];        // thermal-field scale of the column
-        unsigned scol[P];    // site index of the column on plane 0
-        int ocol[P];         // storage slot of the column on plane 0
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int e = tid + j * NT;
-            pos[j] = -1;
-            inner[j] = false;
-            sig[j] = 0.f;
-            scol[j] = 0;
-            ocol[j] = 0;
-            if (e < n_act) {
-                const int p = a.lists[W.list_off + e];
-                pos[j] = p;
-                inner[j] = e < n_int;
-                bool ok = true;
-                const int wx = wrap_coord(W.x0 - 2 + p % WS, nx, a.per[0], ok);
-                const int wy = wrap_coord(W.y0 - 2 + p / WS, ny, a.per[1], ok);
-                const float T = temperature_f(R, (wx + 0.5f) * a.ax, (wy + 0.5f) * a.ay, t);
-                sig[j] = a.sig0 * sqrtf(T);
-                scol[j] = (unsigned)wx + (unsigned)nx * (unsigned)wy;
-                ocol[j] = (int)off + wx + px * wy;
-            }
+        // this thread's list entry (site and storage indices fit in 32 bits: a replica has at
+        // most 2^30 sites and the storage fewer than 2^28 slots)
+        const bool act = tid < n_act;
+        bool inner = false;  // interior column: corrected by this thread
+        int c = 0;           // staged-region position
+        float sig = 0.f;     // thermal-field scale of the column
+        unsigned scol = 0;   // site index of the column on plane 0
+        int ocol = 0;        // storage slot of the column on plane 0
+        if (act) {
+            const unsigned e = a.lists[W.list_off + tid];
+            c = (int)(e & 0x7fffu);
+            inner = (e & 0x8000u) != 0;
+            bool ok = true;
+            const int wx = wrap_coord(xs + c % SW, nx, a.per[0], ok);
+            const int wy = wrap_coord(ys + c / SW, ny, a.per[1], ok);
+            const float T = temperature_f(R, (wx + 0.5f) * a.ax, (wy + 0.5f) * a.ay, t);
+            sig = a.sig0 * sqrtf(T);
+            scol = (unsigned)wx + (unsigned)nx * (unsigned)wy;
+            ocol = off + wx + px * wy;
         }
-        // staged positions of this thread: column offsets within a plane, -1 if outside
+        // per-position copies (fallback): column offsets within a plane (-1: zero-filled,
+        // -2: outside the block's staged region)
         int lofs[LPT];
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             const int idx = tid + l * NT;
-            lofs[l] = -1;
-            if (idx < SA) {
+            const int sx = idx % SW, sy = idx / SW;
+            lofs[l] = -2;
+            if (!tma && idx < CAPS && sx < bx + 4 && sy < by + 4) {
                 bool ok = true;
-                const int cx = wrap_coord(W.x0 - 2 + idx % WS, nx, a.per[0], ok);
-                const int cy = wrap_coord(W.y0 - 2 + idx / WS, ny, a.per[1], ok);
-                if (ok) lofs[l] = cx + px * cy;
+                const int cx = wrap_coord(xs + sx, nx, a.per[0], ok);
+                const int cy = wrap_coord(ys + sy, ny, a.per[1], ok);
+                lofs[l] = ok ? cx + px * cy : -1;
             }
         }
-        float pre[LPT][3];
-        uint16_t preg[LPT];
-        auto fetch = [&](int p) {
+        // stage plane p into ring slot p mod 4 (planes beyond nz + 1 are never needed)
+        auto issue = [&](int p) {
+            if (p > nz + 1) return;
+            const int slot = (p + 4) & 3;
+            float *dst = sS + slot * SLOT_F;
             bool ok = true;
             const int z = wrap_coord(p, nz, a.per[2], ok);
-            const int base = (int)off + z * plane;
-#pragma unroll
-            for (int l = 0; l < LPT; ++l) {
-                if (ok && lofs[l] >= 0) {
-                    const int j = base + lofs[l];
-                    pre[l][0] = __ldg(Sin + j);
-                    pre[l][1] = __ldg(Sin + NS + j);
-                    pre[l][2] = __ldg(Sin + 2 * NS + j);
-                    preg[l] = __ldg(a.gcode + j);
+            if (tma) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_expect_tx(&s_bar[slot], 3u * CAPS * 4u);
+                    // an out-of-range plane of an open lattice: every element is zero-filled
+                    tma_load_4d(dst, map, xs, ys, ok ? z : -2, 0, &s_bar[slot]);
                 } else {
-                    pre[l][0] = pre[l][1] = pre[l][2] = 0.0f;
-                    preg[l] = 0;
+                    mbar_arrive(&s_bar[slot]);
                 }
+            } else {
+                const int base = off + z * plane;
+                uint16_t *gd = sG + slot * CAPS;
+#pragma unroll
+                for (int l = 0; l < LPT; ++l) {
+                    if (lofs[l] == -2) continue;
+                    const int idx = tid + l * NT;
+                    const bool v = ok && lofs[l] >= 0;
+                    const float *src = Sin + (v ? base + lofs[l] : 0);
+                    cp_async4(dst + idx, src, v);
+                    cp_async4(dst + CAPS + idx, src + NS, v);
+                    cp_async4(dst + 2 * CAPS + idx, src + 2 * NS, v);
+                    if (mask) gd[idx] = v ? __ldg(a.gcode + base + lofs[l]) : (uint16_t)0;
+                }
+                mbar_arrive_cp_async(&s_bar[slot]);
             }
         };
-        auto stage = [&](int p) {
-            float *dst = sS + (p & 1) * 3 * CAPS;
-            uint16_t *gd = sG + (p & 3) * CAPS;
-#pragma unroll
-            for (int l = 0; l < LPT; ++l) {
-                const int idx = tid + l * NT;
-                if (idx < SA) {
-                    dst[idx] = pre[l][0];
-                    dst[CAPS + idx] = pre[l][1];
-                    dst[2 * CAPS + idx] = pre[l][2];
-                    gd[idx] = preg[l];
-                }
+        // wait until plane p has landed in its slot; a wait that runs out is recorded here and
+        // acted on at the next barrier vote
+        bool bad = false;
+        auto await = [&](int p) {
+            const int slot = (p + 4) & 3;
+            if (!mbar_wait(&s_bar[slot], (ph >> slot) & 1u)) {
+                bad = true;
+                atomicOr(&a.ctl->err, 2);
             }
+            ph ^= 1u << slot;
         };
 
         const float bapp = R.fB0 * field_polarity_f(R, a.bits, t);
         const float bax = bapp * R.fdir[0], bay = bapp * R.fdir[1], baz = bapp * R.fdir[2];
         const unsigned site_plane = (unsigned)nx * (unsigned)ny;
-        const float q = a.pref * a.dt;
 
-        // prologue: planes -2 and -1 staged, own S and grain code of plane -2 read
-        fetch(-2);
-        stage(-2);
-        fetch(-1);
-        stage(-1);
-        __syncthreads();
-        float Sm1[P][3];           // S on plane k-1 at this column
-        unsigned gm1[P], gm2[P];   // grain codes on planes k-1 and k-2
-        float f1[P][3], th[P][3];  // dt f(S, B(S)) and thermal field of plane k-1
-        int acc[P][3], gacc[P];    // fixed-point record sums of this column
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int p = pos[j] < 0 ? 0 : pos[j];
-            Sm1[j][0] = sS[p];  // plane -2 sits in S slot 0 and grain slot 2
-            Sm1[j][1] = sS[CAPS + p];
-            Sm1[j][2] = sS[2 * CAPS + p];
-            gm1[j] = pos[j] < 0 ? 0u : sG[2 * CAPS + p];
-            gm2[j] = 0;
-            f1[j][0] = f1[j][1] = f1[j][2] = 0.f;
-            th[j][0] = th[j][1] = th[j][2] = 0.f;
-            acc[j][0] = acc[j][1] = acc[j][2] = 0;
-            gacc[j] = -1;
+        // prologue: planes -2 .. 1 staged; own S (and grain code) of plane -2 read
+        issue(-2);
+        issue(-1);
+        issue(0);
+        issue(1);
+        await(-2);
+        await(-1);
+        await(0);
+        float m1x = 0.f, m1y = 0.f, m1z = 0.f;     // S on plane k-1 at this column
+        unsigned gm1 = 0;                           // its grain code (masked replicas)
+        float f1x = 0.f, f1y = 0.f, f1z = 0.f;     // dt f(S, B(S)) of plane k-1
+        float thx = 0.f, thy = 0.f, thz = 0.f;     // thermal field of plane k-1
+        int ax_ = 0, ay_ = 0, az_ = 0, gacc = -1;  // fixed-point record sums of this column
+        if (act) {
+            const float *S2 = sS + 2 * SLOT_F;  // plane -2 sits in slot 2
+            m1x = S2[c];
+            m1y = S2[CAPS + c];
+            m1z = S2[2 * CAPS + c];
+            gm1 = sG[2 * CAPS + c];
         }
-        __syncthreads();
-        fetch(0);
-        stage(0);
-        __syncthreads();
+        // plane -2's slot is restaged by the first march step; plain grain-code stores become visible
+        stop = __syncthreads_or(bad) != 0;
 
-        for (int k = -1; k <= nz; ++k) {
-            fetch(k + 2);
+        // one march step; PH fixes the ring slots: plane k sits in slot (PH + 3) % 4
+        auto march = [&](auto PHC, int k) {
+            constexpr int PH = decltype(PHC)::value;
+            constexpr int SK = (PH + 3) & 3, SK1 = PH & 3, SKM1 = (PH + 2) & 3, SKM2 = (PH + 1) & 3;
+            issue(k + 3);  // into slot (k + 3) mod 4 = SKM1, left by plane k-1 (kept in registers)
+            if (k >= 0) await(k + 1);  // plane 0 was awaited by the prologue
             // ---- predictor on plane k
-            const float *P0 = sS + (k & 1) * 3 * CAPS, *Pp = sS + ((k + 1) & 1) * 3 * CAPS;
-            const uint16_t *G0 = sG + ((k + 4) & 3) * CAPS, *Gp = sG + ((k + 5) & 3) * CAPS;
-            float *Pw = sP + ((k + 3) % 3) * 3 * CAPS;
             bool zok = true;
             const int wz = wrap_coord(k, nz, a.per[2], zok);
-            float S0[P][3];
-            unsigned g0[P];
-            float nf1[P][3], nth[P][3];
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                const int c = pos[j];
-                nf1[j][0] = nf1[j][1] = nf1[j][2] = 0.f;
-                nth[j][0] = nth[j][1] = nth[j][2] = 0.f;
-                S0[j][0] = S0[j][1] = S0[j][2] = 0.f;
-                g0[j] = 0;
-                if (c < 0) continue;
-                g0[j] = G0[c];
-                const float sx = P0[c], sy = P0[CAPS + c], sz = P0[2 * CAPS + c];
-                S0[j][0] = sx;
-                S0[j][1] = sy;
-                S0[j][2] = sz;
-                float npx = 0.f, npy = 0.f, npz = 0.f;
-                if (zok && g0[j] != 0) {
-                    float ex, ey, ez;
-                    if (!mask) {
-                        ex = P0[c - 1] + P0[c + 1] + P0[c - WS] + P0[c + WS] + Sm1[j][0] + Pp[c];
-                        ey = P0[CAPS + c - 1] + P0[CAPS + c + 1] + P0[CAPS + c - WS] + P0[CAPS + c + WS] + Sm1[j][1] +
-                             Pp[CAPS + c];
-                        ez = P0[2 * CAPS + c - 1] + P0[2 * CAPS + c + 1] + P0[2 * CAPS + c - WS] +
-                             P0[2 * CAPS + c + WS] + Sm1[j][2] + Pp[2 * CAPS + c];
-                    } else {
-                        const unsigned g = g0[j];
-                        const float w0 = G0[c - 1] == g, w1 = G0[c + 1] == g, w2 = G0[c - WS] == g,
-                                    w3 = G0[c + WS] == g, w4 = gm1[j] == g, w5 = Gp[c] == g;
-                        ex = w0 * P0[c - 1] + w1 * P0[c + 1] + w2 * P0[c - WS] + w3 * P0[c + WS] + w4 * Sm1[j][0] +
-                             w5 * Pp[c];
-                        ey = w0 * P0[CAPS + c - 1] + w1 * P0[CAPS + c + 1] + w2 * P0[CAPS + c - WS] +
-                             w3 * P0[CAPS + c + WS] + w4 * Sm1[j][1] + w5 * Pp[CAPS + c];
-                        ez = w0 * P0[2 * CAPS + c - 1] + w1 * P0[2 * CAPS + c + 1] + w2 * P0[2 * CAPS + c - WS] +
-                             w3 * P0[2 * CAPS + c + WS] + w4 * Sm1[j][2] + w5 * Pp[2 * CAPS + c];
-                    }
+            const float *P0 = sS + SK * SLOT_F + c, *Pp = sS + SK1 * SLOT_F + c;
+            const float sx = P0[0], sy = P0[CAPS], sz = P0[2 * CAPS];
+            unsigned g0 = 0;
+            float nf1x = 0.f, nf1y = 0.f, nf1z = 0.f, nthx = 0.f, nthy = 0.f, nthz = 0.f;
+            if (act) {
+                float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (mask) g0 = sG[SK * CAPS + c];
+                const bool mag = mask ? g0 != 0 : nonzero3(sx, sy, sz);
+                if (zok && mag) {
                     float n0, n1, n2;
-                    normals3(philox10_rk(philox_ctr(scol[j] + site_plane * (unsigned)wz, (unsigned long long)step),
-                                         s_rk),
+                    normals3(philox10_rk(philox_ctr(scol + site_plane * (unsigned)wz, (unsigned long long)step), s_rk),
                              n0, n1, n2);
-                    const float tx = sig[j] * n0, ty = sig[j] * n1, tz = sig[j] * n2;
-                    nth[j][0] = tx;
-                    nth[j][1] = ty;
-                    nth[j][2] = tz;
-                    const float bx_ = fmaf(a.cJ, ex, bax + tx);
-                    const float by_ = fmaf(a.cJ, ey, bay + ty);
-                    const float bz_ = fmaf(a.cJ, ez, fmaf(a.cK, sz, baz + tz));
-                    const float cx = sy * bz_ - sz * by_, cy = sz * bx_ - sx * bz_, cz = sx * by_ - sy * bx_;
-                    const float sb = sx * bx_ + sy * by_ + sz * bz_, ss = sx * sx + sy * sy + sz * sz;
-                    nf1[j][0] = q * (cx + a.alpha * (sb * sx - ss * bx_));
-                    nf1[j][1] = q * (cy + a.alpha * (sb * sy - ss * by_));
-                    nf1[j][2] = q * (cz + a.alpha * (sb * sz - ss * bz_));
-                    npx = sx + nf1[j][0];
-                    npy = sy + nf1[j][1];
-                    npz = sz + nf1[j][2];
-                    const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
-                    npx *= inv;
-                    npy *= inv;
-                    npz *= inv;
-                }
-                Pw[c] = npx;
-                Pw[CAPS + c] = npy;
-                Pw[2 * CAPS + c] = npz;
-            }
-            __syncthreads();
-
-            // ---- corrector on plane k-1
-            const int kc = k - 1;
-            if (kc >= 0 && kc < nz) {
-                const float *Q = sP + ((kc + 3) % 3) * 3 * CAPS, *Qm = sP + ((kc + 2) % 3) * 3 * CAPS,
-                            *Qp = sP + ((kc + 4) % 3) * 3 * CAPS;
-                const uint16_t *Gc = sG + ((kc + 4) & 3) * CAPS;
-#pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    const int c = pos[j];
-                    const unsigned g = gm1[j];
-                    if (c < 0 || !inner[j] || g == 0) continue;
-                    const float sx = Q[c], sy = Q[CAPS + c], sz = Q[2 * CAPS + c];
+                    nthx = sig * n0;
+                    nthy = sig * n1;
+                    nthz = sig * n2;
                     float ex, ey, ez;
                     if (!mask) {
-                        ex = Q[c - 1] + Q[c + 1] + Q[c - WS] + Q[c + WS] + Qm[c] + Qp[c];
-                        ey = Q[CAPS + c - 1] + Q[CAPS + c + 1] + Q[CAPS + c - WS] + Q[CAPS + c + WS] + Qm[CAPS + c] +
-                             Qp[CAPS + c];
-                        ez = Q[2 * CAPS + c - 1] + Q[2 * CAPS + c + 1] + Q[2 * CAPS + c - WS] + Q[2 * CAPS + c + WS] +
-                             Qm[2 * CAPS + c] + Qp[2 * CAPS + c];
+                        ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x + Pp[0]);
+                        ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y + Pp[CAPS]);
+                        ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
+                             (m1z + Pp[2 * CAPS]);
                     } else {
-                        const float w0 = Gc[c - 1] == g, w1 = Gc[c + 1] == g, w2 = Gc[c - WS] == g,
-                                    w3 = Gc[c + WS] == g, w4 = gm2[j] == g, w5 = g0[j] == g;
-                        ex = w0 * Q[c - 1] + w1 * Q[c + 1] + w2 * Q[c - WS] + w3 * Q[c + WS] + w4 * Qm[c] + w5 * Qp[c];
-                        ey = w0 * Q[CAPS + c - 1] + w1 * Q[CAPS + c + 1] + w2 * Q[CAPS + c - WS] +
-                             w3 * Q[CAPS + c + WS] + w4 * Qm[CAPS + c] + w5 * Qp[CAPS + c];
-                        ez = w0 * Q[2 * CAPS + c - 1] + w1 * Q[2 * CAPS + c + 1] + w2 * Q[2 * CAPS + c - WS] +
-                             w3 * Q[2 * CAPS + c + WS] + w4 * Qm[2 * CAPS + c] + w5 * Qp[2 * CAPS + c];
+                        const uint16_t *G0 = sG + SK * CAPS + c;
+                        const float w0 = G0[-1] == g0, w1 = G0[1] == g0, w2 = G0[-SW] == g0, w3 = G0[SW] == g0,
+                                    w4 = gm1 == g0, w5 = sG[SK1 * CAPS + c] == g0;
+                        ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x + w5 * Pp[0];
+                        ey = w0 * P0[CAPS - 1] + w1 * P0[CAPS + 1] + w2 * P0[CAPS - SW] + w3 * P0[CAPS + SW] +
+                             w4 * m1y + w5 * Pp[CAPS];
+                        ez = w0 * P0[2 * CAPS - 1] + w1 * P0[2 * CAPS + 1] + w2 * P0[2 * CAPS - SW] +
+                             w3 * P0[2 * CAPS + SW] + w4 * m1z + w5 * Pp[2 * CAPS];
                     }
-                    const float bx_ = fmaf(a.cJ, ex, bax + th[j][0]);
-                    const float by_ = fmaf(a.cJ, ey, bay + th[j][1]);
-                    const float bz_ = fmaf(a.cJ, ez, fmaf(a.cK, sz, baz + th[j][2]));
-                    const float cx = sy * bz_ - sz * by_, cy = sz * bx_ - sx * bz_, cz = sx * by_ - sy * bx_;
-                    const float sb = sx * bx_ + sy * by_ + sz * bz_, ss = sx * sx + sy * sy + sz * sz;
-                    const float f2x = q * (cx + a.alpha * (sb * sx - ss * bx_));
-                    const float f2y = q * (cy + a.alpha * (sb * sy - ss * by_));
-                    const float f2z = q * (cz + a.alpha * (sb * sz - ss * bz_));
-                    float ox = Sm1[j][0] + 0.5f * (f1[j][0] + f2x);
-                    float oy = Sm1[j][1] + 0.5f * (f1[j][1] + f2y);
-                    float oz = Sm1[j][2] + 0.5f * (f1[j][2] + f2z);
+                    heun_rhs(a, sx, sy, sz, ex, ey, ez, bax, bay, baz, nthx, nthy, nthz, q, nf1x, nf1y, nf1z);
+                    const float npx = sx + nf1x, npy = sy + nf1y, npz = sz + nf1z;
+                    const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
+                    sp = make_float4(npx * inv, npy * inv, npz * inv, __uint_as_float(g0));
+                }
+                sP[SK * CAPS + c] = sp;
+            }
+            stop = __syncthreads_or(bad) != 0;  // the step's one barrier, and the failure vote
+            // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1), k (SK)
+            const int kc = k - 1;
+            if (inner && kc >= 0 && kc < nz) {
+                const float4 *Q = sP + SKM1 * CAPS + c;
+                const float4 v = Q[0];
+                if (nonzero3(v.x, v.y, v.z)) {
+                    const float4 l = Q[-1], r = Q[1], d = Q[-SW], u = Q[SW];
+                    const float4 zm = sP[SKM2 * CAPS + c], zp = sP[SK * CAPS + c];
+                    float ex, ey, ez;
+                    if (!mask) {
+                        ex = ((l.x + r.x) + (d.x + u.x)) + (zm.x + zp.x);
+                        ey = ((l.y + r.y) + (d.y + u.y)) + (zm.y + zp.y);
+                        ez = ((l.z + r.z) + (d.z + u.z)) + (zm.z + zp.z);
+                    } else {
+                        const unsigned g = __float_as_uint(v.w);
+                        const float w0 = __float_as_uint(l.w) == g, w1 = __float_as_uint(r.w) == g,
+                                    w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u.w) == g,
+                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(zp.w) == g;
+                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u.x + w4 * zm.x + w5 * zp.x;
+                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u.y + w4 * zm.y + w5 * zp.y;
+                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u.z + w4 * zm.z + w5 * zp.z;
+                    }
+                    float f2x, f2y, f2z;
+                    heun_rhs(a, v.x, v.y, v.z, ex, ey, ez, bax, bay, baz, thx, thy, thz, q, f2x, f2y, f2z);
+                    float ox = m1x + 0.5f * (f1x + f2x);
+                    float oy = m1y + 0.5f * (f1y + f2y);
+                    float oz = m1z + 0.5f * (f1z + f2z);
                     const float inv = rsqrtf(ox * ox + oy * oy + oz * oz);
                     ox *= inv;
                     oy *= inv;
                     oz *= inv;
-                    const int o = ocol[j] + kc * plane;
+                    const int o = ocol + kc * plane;
                     Sout[o] = ox;
                     Sout[NS + o] = oy;
                     Sout[2 * NS + o] = oz;
                     if (RECORD) {
+                        const unsigned g = mask ? __float_as_uint(v.w) : (unsigned)__ldg(a.gcode + o);
                         const int gg = R.grain_off + (int)g - 1;
-                        if (gg != gacc[j] || (kc & 63) == 63) {
-                            if (gacc[j] >= 0) {
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 0, (unsigned long long)(long long)acc[j][0]);
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 1, (unsigned long long)(long long)acc[j][1]);
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 2, (unsigned long long)(long long)acc[j][2]);
+                        if (gg != gacc || (kc & 63) == 63) {
+                            if (gacc >= 0) {
+                                atomicAdd(a.grain_fx + 3 * gacc + 0, (unsigned long long)(long long)ax_);
+                                atomicAdd(a.grain_fx + 3 * gacc + 1, (unsigned long long)(long long)ay_);
+                                atomicAdd(a.grain_fx + 3 * gacc + 2, (unsigned long long)(long long)az_);
                             }
-                            gacc[j] = gg;
-                            acc[j][0] = acc[j][1] = acc[j][2] = 0;
+                            gacc = gg;
+                            ax_ = ay_ = az_ = 0;
                         }
-                        acc[j][0] += __float2int_rn(ox * FX_SCALE);
-                        acc[j][1] += __float2int_rn(oy * FX_SCALE);
-                        acc[j][2] += __float2int_rn(oz * FX_SCALE);
+                        ax_ += __float2int_rn(ox * FX_SCALE);
+                        ay_ += __float2int_rn(oy * FX_SCALE);
+                        az_ += __float2int_rn(oz * FX_SCALE);
                     }
                 }
             }
             // carry this column's plane-k values to the next march step
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                gm2[j] = gm1[j];
-                gm1[j] = g0[j];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    Sm1[j][d] = S0[j][d];
-                    f1[j][d] = nf1[j][d];
-                    th[j][d] = nth[j][d];
-                }
-            }
-            stage(k + 2);
-            __syncthreads();
+            m1x = sx;
+            m1y = sy;
+            m1z = sz;
+            gm1 = g0;
+            f1x = nf1x;
+            f1y = nf1y;
+            f1z = nf1z;
+            thx = nthx;
+            thy = nthy;
+            thz = nthz;
+        };
+
+        // k runs from -1 to nz; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
+        int kend = -2;  // last march step run
+        for (int kb = -1; kb <= nz && !stop; kb += 4) {
+            march(IC<0>(), kb);
+            kend = kb;
+            if (!stop && kb + 1 <= nz) march(IC<1>(), kend = kb + 1);
+            if (!stop && kb + 2 <= nz) march(IC<2>(), kend = kb + 2);
+            if (!stop && kb + 3 <= nz) march(IC<3>(), kend = kb + 3);
         }
-        if (RECORD) {
-#pragma unroll
-            for (int j = 0; j < P; ++j)
-                grain_accumulate_fx(a.grain_fx, gacc[j], acc[j][0], acc[j][1], acc[j][2], gacc[j] >= 0);
+        if (stop) {
+            // give the fills issued after the last awaited plane a bounded time to land before
+            // the CTA's shared memory is released
+            if (tid == 0)
+                for (int p = max(kend + 2, 1); p <= min(kend + 3, nz + 1); ++p) await(p);
+            return;  // uniform: every thread saw the same vote
         }
+        if (RECORD) grain_accumulate_fx(a.grain_fx, gacc, ax_, ay_, az_, gacc >= 0);
+        __syncthreads();  // all reads of this item's slots are done before they are re-armed
     }
 }
 
 // Opt in to the variant's dynamic shared memory (done before any stream capture, when the
 // work list is built).
-template <int NT, int P, int CAPS>
+template <int NT, int SW, int SH>
 static cudaError_t ensure_attrs() {
-    using Sh = FusedShape<NT, P, CAPS>;
+    using Sh = FusedShape<NT, SW, SH>;
     static bool init = false;
     if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<NT, P, CAPS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<NT, SW, SH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Sh::smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused<NT, P, CAPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_fused<NT, SW, SH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Sh::smem);
         if (e != cudaSuccess) return e;
         init = true;
@@ -369,46 +448,50 @@ static cudaError_t ensure_attrs() {
     return cudaSuccess;
 }
 
-template <int NT, int P, int CAPS>
+template <int NT, int SW, int SH>
 static cudaError_t launch_variant(const FusedArgs &a, int grid, bool record, cudaStream_t st) {
-    using Sh = FusedShape<NT, P, CAPS>;
-    cudaError_t e = ensure_attrs<NT, P, CAPS>();
+    using Sh = FusedShape<NT, SW, SH>;
+    cudaError_t e = ensure_attrs<NT, SW, SH>();
     if (e != cudaSuccess) return e;
     if (record)
-        k_fused<NT, P, CAPS, true><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<NT, SW, SH, true><<<grid, NT, Sh::smem, st>>>(a);
     else
-        k_fused<NT, P, CAPS, false><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<NT, SW, SH, false><<<grid, NT, Sh::smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NT, int P, int CAPS>
+template <int NT, int SW, int SH>
 static int blocks_per_sm() {
-    using Sh = FusedShape<NT, P, CAPS>;
+    using Sh = FusedShape<NT, SW, SH>;
     int n = 0;
-    if (ensure_attrs<NT, P, CAPS>() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<NT, P, CAPS, false>, NT, Sh::smem) != cudaSuccess)
+    if (ensure_attrs<NT, SW, SH>() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<NT, SW, SH, false>, NT, Sh::smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-// compiled variants: threads per CTA, list entries per thread, staged positions per plane
-#define HAMR_FUSED_VARIANTS(X) X(0, 1024, 1, 1536) X(1, 512, 1, 768) X(2, 1024, 1, 1280) X(3, 256, 2, 768)
+// compiled variants: threads per CTA and the staged region's pitch x rows (pitch a multiple
+// of 4 so that TMA rows are 16-byte multiples).  A block of bx x by columns fits when
+// bx + 4 <= pitch (bx + 7 with TMA, whose origin is rounded down to a multiple of 4),
+// by + 4 <= rows and it lists at most one column per thread.
+#define HAMR_FUSED_VARIANTS(X) X(0, 1024, 68, 24) X(1, 512, 36, 24) X(2, 256, 36, 14) X(3, 1024, 36, 40)
 
 cudaError_t launch_fused_step(int v, const FusedArgs &a, int grid, bool record, cudaStream_t st) {
-#define X(I, NT, P, C) \
-    if (v == I) return launch_variant<NT, P, C>(a, grid, record, st);
+#define X(I, NT, SW, SH) \
+    if (v == I) return launch_variant<NT, SW, SH>(a, grid, record, st);
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
 bool fused_variant(int v, FusedVariant &out) {
-#define X(I, NT, P, C)      \
-    if (v == I) {           \
-        out.threads = NT;   \
-        out.per_thread = P; \
-        out.staged = C;     \
-        return true;        \
+#define X(I, NT, SW, SH)      \
+    if (v == I) {             \
+        out.threads = NT;     \
+        out.pitch = SW;       \
+        out.rows = SH;        \
+        out.staged = SW * SH; \
+        return true;          \
     }
     HAMR_FUSED_VARIANTS(X)
 #undef X
@@ -416,8 +499,8 @@ bool fused_variant(int v, FusedVariant &out) {
 }
 
 int fused_max_blocks_per_sm(int v) {
-#define X(I, NT, P, C) \
-    if (v == I) return blocks_per_sm<NT, P, C>();
+#define X(I, NT, SW, SH) \
+    if (v == I) return blocks_per_sm<NT, SW, SH>();
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return 0;

@@ -116,7 +116,7 @@ def test_fp32_sc32_pbc_thermal_1000():
     assert max_abs(Mg, Mo) < TOL32
 
 
-TILES = [(1024, 1536), (512, 768), (1024, 1280), (256, 768)]
+TILES = [(1024, 68 * 24), (512, 36 * 24), (256, 36 * 14), (1024, 36 * 40)]
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -185,6 +185,27 @@ def test_fp32_non_columnar_grains():
         (gg, o, Mg, Mo), = run_both(w, 150, record_every=50)
         assert max_abs(gg, o) < tol, prec
         assert max_abs(Mg, Mo) < tol, prec
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_fp32_many_items_per_cta(tile):
+    """More column blocks than resident CTAs, so that every persistent CTA runs several work
+    items in a row (open edges: TMA staging), mixed with a replica that needs the exchange mask
+    (per-position staging) in the same launch."""
+    rng = np.random.default_rng(9)
+    reps = []
+    for r in range(200):
+        nx, ny, nz = (int(v) for v in rng.integers([10, 10, 2], [23, 23, 7]))
+        reps.append(dict(dims=(nx, ny, nz), seed=500 + r, init="random", T=dict(T_amb=float(rng.uniform(100, 900))),
+                         field=dict(B0=0.7, direction=(0, 0, -1))))
+    g = np.zeros((12, 14), np.int32)
+    g[:, 7:] = 1
+    reps.append(dict(dims=(14, 12, 3), seed=777, grain=I.columnar(g, 3), n_grains=2, init="random",
+                     T=dict(T_amb=300.0)))
+    w = workload_of(reps)
+    for r, (gg, o, Mg, Mo) in enumerate(run_both(w, 40, record_every=20, tile=tile)):
+        assert max_abs(gg, o) < TOL32, r
+        assert max_abs(Mg, Mo) < TOL32, r
 
 
 def test_periodic_tiny_lattices_both_precisions():
