@@ -1,0 +1,134 @@
+"""Statistical checks of the GPU path at T > 0 against what the physics fixes.
+
+  * single spins (no exchange) sample the Boltzmann distribution: <S_z> = L(mu_s B / kB T)
+    in a field (the Langevin function of Sec. II), <S_z^2> in uniaxial anisotropy, and the
+    uniform sphere with neither;
+  * the classical simple-cubic Heisenberg ferromagnet orders at kB T_C = 1.443 J (Monte Carlo
+    value, Chen, Ferrenberg and Landau 1993; Eq. 8 of the paper with eps_SC = 0.72 gives the
+    same 1.44): the Binder cumulants U4 = 1 - <m^4> / (3 <m^2>^2) of periodic L^3 cubes of
+    several sizes cross at T_C, which must come out within 1 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2502_02236_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+KB = 1.380649e-23
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_02236_gb300 import build
+    build.build()
+
+
+def langevin(x):
+    return 1 / math.tanh(x) - 1 / x
+
+
+def spin_ensemble(precision, B0, ku, T, n=8192, steps=9000, burn=3000, every=100, dt=1e-16, alpha=1.0):
+    """S_z samples of n independent spins (J = 0) after a burn-in."""
+    from paper_2502_02236_gb300.hamr import Lattice
+    with Lattice([(n, 1, 1)], [4242], precision=precision, a=0.25e-9, mu_s=I.MU_S, ku=ku, alpha=alpha,
+                 dt=dt) as lat:
+        lat.set_neighbour_shells([0.0])
+        lat.set_temperature_profile(0, T)
+        lat.set_field_sequence(0, B0, (0, 0, 1))
+        lat.sllg_heun_steps(burn)
+        z = []
+        for _ in range((steps - burn) // every):
+            lat.sllg_heun_steps(every)
+            z.append(lat.read_moments(0)[:, 2].copy())
+    return np.array(z)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_langevin_in_field(precision):
+    T, x = 300.0, 2.0
+    B0 = x * KB * T / I.MU_S
+    z = spin_ensemble(precision, B0, 0.0, T, n=8192 if precision == "fp32" else 2048)
+    err = z.std() / math.sqrt(z.size / 4)
+    assert abs(z.mean() - langevin(x)) < 5 * err + 0.01, (z.mean(), langevin(x), err)
+
+
+def test_boltzmann_in_anisotropy():
+    from scipy import integrate
+    T, s = 300.0, 3.0
+    ku = s * KB * T
+    z = spin_ensemble("fp32", 0.0, ku, T)
+    Z = 2 * integrate.quad(lambda x: math.exp(s * x * x), 0, 1)[0]
+    want = math.exp(s) / (s * Z) - 1 / (2 * s)
+    z2 = z ** 2
+    err = z2.std() / math.sqrt(z2.size / 4)
+    assert abs(z2.mean() - want) < 5 * err + 0.01, (z2.mean(), want, err)
+
+
+def test_isotropic_sphere():
+    z = spin_ensemble("fp32", 0.0, 0.0, 300.0)
+    err = 1 / math.sqrt(3 * z.size / 4)
+    assert abs(z.mean()) < 5 * err + 0.01
+    assert abs((z ** 2).mean() - 1 / 3) < 5 * err + 0.01
+
+
+def binder_run(sizes, temps, seeds, steps, burn, every, dt, alpha=1.0):
+    """U4 and its standard error for every (L, T): periodic L^3 cubes, J = 6.7e-21 J, no
+    anisotropy or field, all replicas in one FP32 launch."""
+    from paper_2502_02236_gb300.hamr import Lattice
+    reps = [(L, T, s) for L in sizes for T in temps for s in range(seeds)]
+    dims = [(L, L, L) for (L, T, s) in reps]
+    lat = Lattice(dims, [1000 + i for i in range(len(reps))], precision="fp32", a=0.25e-9,
+                  periodic=(True, True, True), mu_s=I.MU_S, ku=0.0, alpha=alpha, dt=dt)
+    lat.set_neighbour_shells([I.J_SC])
+    for r, (L, T, s) in enumerate(reps):
+        lat.set_temperature_profile(r, T)
+    lat.sllg_heun_steps(burn)
+    lat.clear_records()
+    lat.sllg_heun_steps(steps, every)
+    out = {}
+    for r, (L, T, s) in enumerate(reps):
+        M, st, _ = lat.read_magnetisation(r)
+        m2 = (M ** 2).sum(axis=1)
+        out.setdefault((L, T), []).append(m2)
+    lat.close()
+    res = {}
+    for key, chains in out.items():
+        m2 = np.concatenate(chains)
+        # error from the spread between independent chains
+        u_chain = [1 - (c ** 2).mean() / (3 * c.mean() ** 2) for c in chains]
+        res[key] = (1 - (m2 ** 2).mean() / (3 * m2.mean() ** 2), np.std(u_chain) / math.sqrt(len(chains)))
+    return res
+
+
+def crossing(temps, ua, ub):
+    """Temperature where U4 of two sizes cross (linear interpolation of the difference)."""
+    d = np.asarray(ua) - np.asarray(ub)
+    for i in range(len(temps) - 1):
+        if d[i] == 0:
+            return temps[i]
+        if d[i] * d[i + 1] < 0:
+            return temps[i] + (temps[i + 1] - temps[i]) * d[i] / (d[i] - d[i + 1])
+    return None
+
+
+def test_curie_point_binder_crossing():
+    """At the workloads' time step (0.1 fs).  The Heun scheme's O(dt) bias moves the crossing
+    by about +6 K per 0.1 fs of step; at 0.1 fs it stays well inside 1 %."""
+    Tc = 1.443 * I.J_SC / KB  # 700.3 K
+    temps = [Tc * f for f in (0.97, 0.985, 0.995, 1.0, 1.005, 1.015, 1.03)]
+    sizes = (8, 12, 16)
+    res = binder_run(sizes, temps, seeds=10, steps=300000, burn=100000, every=50, dt=1e-16)
+    cross = []
+    for La, Lb in ((8, 12), (8, 16), (12, 16)):
+        t = crossing(temps, [res[(La, T)][0] for T in temps], [res[(Lb, T)][0] for T in temps])
+        assert t is not None, (La, Lb, {k: v for k, v in res.items()})
+        cross.append(t)
+    est = float(np.mean(cross))
+    print("Binder crossings [K]:", cross, "T_C estimate", est, "reference", Tc)
+    assert abs(est / Tc - 1) < 0.01, (cross, est, Tc)
