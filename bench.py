@@ -171,11 +171,31 @@ def kernel_traffic():
     return None
 
 
+def l2_note(n_sites):
+    import torch
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    mb = 12 * n_sites / 1e6
+    if 12 * n_sites > l2:
+        return "inputs larger than L2 (two %.0f MB FP32 state buffers, L2 %.0f MB); no flush" % (mb, l2 / 1e6)
+    return "state fits in L2 (two %.0f MB FP32 buffers, L2 %.0f MB): L2-resident, not flushed" % (mb, l2 / 1e6)
+
+
+def rank_seeds(reps, rank):
+    """Philox keys of one rank's replicas: each rank runs its own ensemble (the workload's
+    seeds with the rank in the top 16 bits), so ranks share no random stream."""
+    return [int(rep["seed"]) ^ (rank << 48) for rep in reps]
+
+
+def aggregate(n_sites, steps, world, ms):
+    """Whole-job spin-steps/s: every rank advanced n_sites sites by `steps` steps, and the
+    job took the slowest rank's time `ms`."""
+    return n_sites * steps * world / (ms / 1e3)
+
+
 def build_lattice(w, precision, rank=0):
-    from paper_2502_02236_gb300 import inputs as I
     from paper_2502_02236_gb300.hamr import Lattice
     reps = w["replicas"]
-    seeds = [int(rep["seed"]) ^ (rank << 48) for rep in reps]
+    seeds = rank_seeds(reps, rank)
     lat = Lattice([rep["dims"] for rep in reps], seeds, lattice=w["lattice"], precision=precision,
                   neighbours=w["neighbours"], a=w["a"], c=w["c"], periodic=w["periodic"], mu_s=w["mu_s"],
                   ku=w["ku"], alpha=w["alpha"], dt=w["dt"])
@@ -217,29 +237,31 @@ def timed(lat, dist, K, record_every):
     return e0.elapsed_time(e1)
 
 
-def cpu_baseline(w, seconds, steps_cap=None):
-    """The FP64 oracle as it stands on this host's cores, over a bounded sample of the
-    workload: whole replicas in order, one step at a time, until `seconds` have passed."""
+def cpu_baseline(w, seconds):
+    """The FP64 oracle as it stands on this host's cores (OpenMP over sites, all cores), over a
+    bounded sample of the workload: the first replicas, whose oracle contexts (neighbour lists)
+    are built before timing, stepped together until about `seconds` have passed."""
     import oracle as orc
-    from paper_2502_02236_gb300 import inputs as I
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from common import initial, oracle_params
-    done_sites = 0
-    steps = 0
-    used = []
-    t0 = time.perf_counter()
+    reps, n = [], 0
     for r, rep in enumerate(w["replicas"]):
-        o = orc.Oracle(oracle_params(w, r), rep.get("grain"))
-        S = initial(rep)
-        n = int(np.prod(rep["dims"]))
-        o.step(S, 0)
-        done_sites += n
-        steps += 1
-        used.append(r)
-        if time.perf_counter() - t0 > seconds or (steps_cap and steps >= steps_cap):
+        reps.append(r)
+        n += int(np.prod(rep["dims"]))
+        if n >= 300000:
             break
+    orcs = [orc.Oracle(oracle_params(w, r), w["replicas"][r].get("grain")) for r in reps]
+    S = [initial(w["replicas"][r]) for r in reps]
+    for o, s in zip(orcs, S):  # one untimed step
+        o.step(s, 0)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for o, s in zip(orcs, S):
+            o.step(s, 1 + steps)
+        steps += 1
     el = time.perf_counter() - t0
-    return done_sites / el, used, el
+    return n * steps / el, reps, n, steps, el
 
 
 def main():
@@ -279,7 +301,7 @@ def main():
     ms = timed(lat, dist, K, rec)
     clk = clocks.stop()
     ms = dist.max(ms)
-    value = n_sites * K * dist.world / (ms / 1e3)
+    value = aggregate(n_sites, K, dist.world, ms)
     # the dominant kernel alone: the same K steps without records (one fused launch per step
     # plus one bookkeeping launch per 64 steps)
     ms_k = dist.max(timed(lat, dist, K, 0))
@@ -294,7 +316,7 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": args.workload, "replicas": len(w["replicas"]), "lattice_sites": n_sites,
                       "magnetic_sites": n_mag, "record_every": rec, "tile": list(tile),
-                      "l2": "inputs larger than L2 (two %.0f MB FP32 state buffers)" % (12 * n_sites / 1e6),
+                      "l2": l2_note(n_sites),
                       "parallelism": "replica batches per GPU, no collective"},
            "magnetic_spin_steps_per_s": n_mag * K * dist.world / (ms / 1e3),
            "gpu_launches": launches,
@@ -343,10 +365,10 @@ def main():
                       "note": "per call: H2D of all spins, K steps, D2H of M(t) and all spins; bytes / K"}
 
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
-        v, used, el = cpu_baseline(w, args.cpu_seconds)
+        v, reps, n, steps, el = cpu_baseline(w, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": "spin-steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": "one FP64 oracle step of replicas 0..%d of the workload (%.1f s)"
-                                         % (used[-1], el)}
+                               "sample": "FP64 oracle, replicas 0..%d of the workload (%d sites), %d steps in %.1f s"
+                                         % (reps[-1], n, steps, el)}
     lat.close()
     if dist.rank == 0:
         print(json.dumps(out), flush=True)

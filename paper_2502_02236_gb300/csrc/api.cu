@@ -975,7 +975,7 @@ int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t 
                           cudaMemcpyHostToDevice, h->stream));
     // both state buffers: the fused kernel never writes non-magnetic sites
     for (int b = 0; b < 2; ++b)
-        if (h->S[b]) CK(h, launch_zero_void(h->prec, h->S[b], h->NS, h->gcode_d, h->stream));
+        if (h->S[b]) CK(h, launch_zero_void(h->prec, h->S[b], h->NS, h->gcode_d, R.off, span, h->stream));
     if (h->nbr == HAMR_NBR_CSR) {
         if (build_ell_replica(h, replica, h->ell_w) != 0) return fail(h, HAMR_ERR_ARG, "neighbour list too wide");
         int rc = upload_ell_replica(h, replica);

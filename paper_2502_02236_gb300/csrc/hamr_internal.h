@@ -124,7 +124,8 @@ cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const Replic
                                unsigned long long *grain_fx, double *grain_last, double *rec, long long rec_cap,
                                long long *rec_step, cudaStream_t st);
 cudaError_t launch_init_state(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
-cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st);
+cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, long long first,
+                             long long count, cudaStream_t st);
 cudaError_t launch_aos_to_soa(int prec, const double *src, void *S, long long NS, const ReplicaDev *reps,
                               int r, const uint16_t *gcode, long long n, cudaStream_t st);
 cudaError_t launch_soa_to_aos(int prec, const void *S, long long NS, const ReplicaDev *reps, int r,

@@ -98,9 +98,9 @@ __global__ void k_init_state(Real *S, long long NS, const uint16_t *gcode) {
 }
 
 template <typename Real>
-__global__ void k_zero_void(Real *S, long long NS, const uint16_t *gcode) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= NS || gcode[j] != 0) return;
+__global__ void k_zero_void(Real *S, long long NS, const uint16_t *gcode, long long first, long long count) {
+    const long long j = first + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= first + count || gcode[j] != 0) return;
     S[j] = Real(0);
     S[NS + j] = Real(0);
     S[2 * NS + j] = Real(0);
@@ -145,11 +145,13 @@ cudaError_t launch_init_state(int prec, void *S, long long NS, const uint16_t *g
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, cudaStream_t st) {
+cudaError_t launch_zero_void(int prec, void *S, long long NS, const uint16_t *gcode, long long first,
+                             long long count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
     if (prec == HAMR_FP64)
-        k_zero_void<double><<<nblk(NS, 256), 256, 0, st>>>((double *)S, NS, gcode);
+        k_zero_void<double><<<nblk(count, 256), 256, 0, st>>>((double *)S, NS, gcode, first, count);
     else
-        k_zero_void<float><<<nblk(NS, 256), 256, 0, st>>>((float *)S, NS, gcode);
+        k_zero_void<float><<<nblk(count, 256), 256, 0, st>>>((float *)S, NS, gcode, first, count);
     return cudaGetLastError();
 }
 

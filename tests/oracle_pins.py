@@ -435,10 +435,72 @@ def check_isotropic_thermal():
 
 
 # checks the mutation test runs (fast ones first)
+# ----------------------------------------------------------------------------- reductions
+def check_energy_closed_form():
+    """Uniform state v: every bond contributes -J_s (v.v = 1) once, so on a lattice with
+    n_s bonds in shell s, E = -sum_s J_s n_s - N ku v_z^2 - N mu_s B.v (Eqs. 2, 3 as an
+    energy).  SC, periodic x,y and open z: 3N - nx ny bonds.  L1_0 fully periodic: per
+    site 2 in-plane nearest, 1 out-of-plane and 2 in-plane diagonal bonds."""
+    v = np.array([0.36, -0.48, 0.8])
+    B0, d = 0.7, np.array([0.6, 0.0, -0.8])
+    nx, ny, nz, J, ku = 5, 4, 3, 6.7e-21, 1e-22
+    p = o.sc_params(nx, ny, nz, A, J, periodic=(True, True, False), ku=ku, mu_s=MU_S, B0=B0,
+                    direction=tuple(d))
+    N = nx * ny * nz
+    want = -J * (3 * N - nx * ny) - N * ku * v[2] ** 2 - N * MU_S * B0 * (d @ v)
+    got = o.Oracle(p).energy(np.tile(v, (N, 1)), 0)
+    assert abs(got - want) < 1e-12 * abs(want), (got, want)
+    J1, J2, J3 = 6.7e-21, 3.35e-21, 0.67e-21
+    p = o.l10_params(6, 6, 4, 0.385e-9, 0.371e-9, J1, J2, J3, periodic=(True, True, True), ku=0.0,
+                     mu_s=MU_S)
+    N = 6 * 6 * 4
+    got = o.Oracle(p).energy(np.tile(v, (N, 1)), 0)
+    want = -N * (2 * J1 + J2 + 2 * J3)
+    assert abs(got - want) < 1e-12 * abs(want), (got, want)
+
+
+def check_magnetisation_and_grain_sums():
+    """M averages the magnetic sites only and the per-grain sums add each grain's spins
+    (Eq. 6 as an average): against brute-force sums on a tiny lattice with voids; a +z
+    state with voids has M = z exactly."""
+    p = o.sc_params(5, 4, 3, A, 6.7e-21)
+    rng = np.random.default_rng(5)
+    grain = rng.integers(-1, 4, size=p.n).astype(np.int32)
+    S = _random_state(p.n, 9)
+    S[grain < 0] = 0.0
+    orc = o.Oracle(p, grain)
+    mag = grain >= 0
+    assert np.allclose(orc.magnetisation(S), S[mag].sum(axis=0) / mag.sum(), rtol=0, atol=1e-15)
+    sums, counts = orc.grain_sums(S, 4)
+    for g in range(4):
+        assert counts[g] == (grain == g).sum()
+        assert np.allclose(sums[g], S[grain == g].sum(axis=0), rtol=0, atol=1e-14)
+    up = np.zeros_like(S)
+    up[mag, 2] = 1.0
+    assert np.array_equal(orc.magnetisation(up), [0.0, 0.0, 1.0])
+
+
+def check_step_sites_matches_full_step():
+    """The site-by-site step used on full-size lattices gives what the whole-lattice step
+    gives, at every site (granular, periodic in x, laser and write field on)."""
+    p = o.sc_params(7, 6, 4, A, 6.7e-21, periodic=(True, False, False), ku=1e-22, alpha=0.1,
+                    dt=1e-16, T_amb=300.0, T_peak=800.0, fwhm=2e-9, x0=1e-9, y0=0.7e-9, vx=2e4,
+                    B0=0.8, direction=(0, 0, -1), seed=3)
+    rng = np.random.default_rng(8)
+    grain = rng.integers(-1, 3, size=p.n).astype(np.int32)
+    S = _random_state(p.n, 10)
+    S[grain < 0] = 0.0
+    want = S.copy()
+    o.Oracle(p, grain).step(want, 5)
+    got = o.step_sites(p, grain, S, 5, np.arange(p.n))
+    assert np.max(np.abs(got - want)) < 1e-15
+
+
 FAST_CHECKS = [
     check_philox_kat, check_larmor, check_damped_relaxation, check_anisotropy_precession,
     check_uniform_state_no_exchange_torque, check_drivers, check_neighbour_geometry,
     check_grain_decoupling, check_spin_waves_sc, check_spin_waves_l10_shells,
     check_conservation_alpha0, check_normals_statistics, check_boltzmann_field,
-    check_boltzmann_anisotropy,
+    check_boltzmann_anisotropy, check_energy_closed_form, check_magnetisation_and_grain_sums,
+    check_step_sites_matches_full_step,
 ]

@@ -36,6 +36,11 @@ MUTANTS = [
     ("grain coupling", "if (grain[j] != grain[i]) continue;", ""),
     ("predictor noise scale", "for (int d = 0; d < 3; ++d) B[d] += Bth[3 * i + d];\n        orc_llg_rhs(p, S + 3 * i",
      "for (int d = 0; d < 3; ++d) B[d] += 2.0 * Bth[3 * i + d];\n        orc_llg_rhs(p, S + 3 * i"),
+    ("magnetisation counts voids", "if (c->grain[i] < 0) continue;\n        for (int d = 0; d < 3; ++d) m[d]",
+     "for (int d = 0; d < 3; ++d) m[d]"),
+    ("energy counts each bond twice", "E -= 0.5 * p->J[c->shell[k]]", "E -= p->J[c->shell[k]]"),
+    ("grain sums drop the last grain", "if (g < 0 || g >= n_grains) continue;",
+     "if (g < 0 || g >= n_grains - 1) continue;"),
 ]
 
 
