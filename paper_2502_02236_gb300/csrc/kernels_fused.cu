@@ -120,19 +120,13 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// dt f(S, B) for B = (J/mu_s) sum of the six neighbours (each weighted 0/1 when masked)
-//                    + (2 ku/mu_s) S_z z + B_app + B_th
-__device__ __forceinline__ void heun_rhs(const FusedArgs &a, float sx, float sy, float sz, float ex, float ey,
-                                         float ez, float bax, float bay, float baz, float tx, float ty, float tz,
-                                         float q, float &fx, float &fy, float &fz) {
-    const float bx = fmaf(a.cJ, ex, bax + tx);
-    const float by = fmaf(a.cJ, ey, bay + ty);
-    const float bz = fmaf(a.cJ, ez, fmaf(a.cK, sz, baz + tz));
+// f(S, B) / (dt pref) = S x B + alpha [(S.B) S - (S.S) B]  (Eq. 1 in Landau-Lifshitz form)
+__device__ __forceinline__ float3 rhs_u(float sx, float sy, float sz, float ss, float bx, float by, float bz,
+                                        float al) {
     const float cx = sy * bz - sz * by, cy = sz * bx - sx * bz, cz = sx * by - sy * bx;
-    const float sb = sx * bx + sy * by + sz * bz, ss = sx * sx + sy * sy + sz * sz;
-    fx = q * (cx + a.alpha * (sb * sx - ss * bx));
-    fy = q * (cy + a.alpha * (sb * sy - ss * by));
-    fz = q * (cz + a.alpha * (sb * sz - ss * bz));
+    const float sb = sx * bx + sy * by + sz * bz;
+    return make_float3(fmaf(al, fmaf(sb, sx, -ss * bx), cx), fmaf(al, fmaf(sb, sy, -ss * by), cy),
+                       fmaf(al, fmaf(sb, sz, -ss * bz), cz));
 }
 
 template <int NT, int SW, int SH, bool RECORD>
@@ -281,16 +275,20 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
         await(-1);
         await(0);
         float m1x = 0.f, m1y = 0.f, m1z = 0.f;     // S on plane k-1 at this column
-        unsigned gm1 = 0;                           // its grain code (masked replicas)
-        float f1x = 0.f, f1y = 0.f, f1z = 0.f;     // dt f(S, B(S)) of plane k-1
-        float thx = 0.f, thy = 0.f, thz = 0.f;     // thermal field of plane k-1
+        float c0x = 0.f, c0y = 0.f, c0z = 0.f;     // S on plane k
+        unsigned gm1 = 0;                           // grain code of plane k-1 (masked replicas)
+        float amx = 0.f, amy = 0.f, amz = 0.f;     // S + dt f(S, B(S)) / 2 of plane k-1
+        float hmx = 0.f, hmy = 0.f, hmz = 0.f;     // B_app + B_th of plane k-1
         int ax_ = 0, ay_ = 0, az_ = 0, gacc = -1;  // fixed-point record sums of this column
         if (act) {
-            const float *S2 = sS + 2 * SLOT_F;  // plane -2 sits in slot 2
+            const float *S2 = sS + 2 * SLOT_F, *S3 = sS + 3 * SLOT_F;  // planes -2 and -1
             m1x = S2[c];
             m1y = S2[CAPS + c];
             m1z = S2[2 * CAPS + c];
             gm1 = sG[2 * CAPS + c];
+            c0x = S3[c];
+            c0y = S3[CAPS + c];
+            c0z = S3[2 * CAPS + c];
         }
         // plane -2's slot is restaged by the first march step; plain grain-code stores become visible
         stop = __syncthreads_or(bad) != 0;
@@ -301,75 +299,82 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
             constexpr int SK = (PH + 3) & 3, SK1 = PH & 3, SKM1 = (PH + 2) & 3, SKM2 = (PH + 1) & 3;
             issue(k + 3);  // into slot (k + 3) mod 4 = SKM1, left by plane k-1 (kept in registers)
             if (k >= 0) await(k + 1);  // plane 0 was awaited by the prologue
-            // ---- predictor on plane k
+            // ---- predictor on plane k (its own S is in c0, carried from the last step)
             bool zok = true;
             const int wz = wrap_coord(k, nz, a.per[2], zok);
             const float *P0 = sS + SK * SLOT_F + c, *Pp = sS + SK1 * SLOT_F + c;
-            const float sx = P0[0], sy = P0[CAPS], sz = P0[2 * CAPS];
+            const float sx = c0x, sy = c0y, sz = c0z;
+            const float ppx = Pp[0], ppy = Pp[CAPS], ppz = Pp[2 * CAPS];
             unsigned g0 = 0;
-            float nf1x = 0.f, nf1y = 0.f, nf1z = 0.f, nthx = 0.f, nthy = 0.f, nthz = 0.f;
+            float anx = 0.f, any = 0.f, anz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+            float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
             if (act) {
-                float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (mask) g0 = sG[SK * CAPS + c];
                 const bool mag = mask ? g0 != 0 : nonzero3(sx, sy, sz);
                 if (zok && mag) {
                     float n0, n1, n2;
                     normals3(philox10_rk(philox_ctr(scol + site_plane * (unsigned)wz, (unsigned long long)step), s_rk),
                              n0, n1, n2);
-                    nthx = sig * n0;
-                    nthy = sig * n1;
-                    nthz = sig * n2;
+                    hx = fmaf(sig, n0, bax);
+                    hy = fmaf(sig, n1, bay);
+                    hz = fmaf(sig, n2, baz);
                     float ex, ey, ez;
                     if (!mask) {
-                        ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x + Pp[0]);
-                        ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y + Pp[CAPS]);
+                        ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x + ppx);
+                        ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y + ppy);
                         ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
-                             (m1z + Pp[2 * CAPS]);
+                             (m1z + ppz);
                     } else {
                         const uint16_t *G0 = sG + SK * CAPS + c;
                         const float w0 = G0[-1] == g0, w1 = G0[1] == g0, w2 = G0[-SW] == g0, w3 = G0[SW] == g0,
                                     w4 = gm1 == g0, w5 = sG[SK1 * CAPS + c] == g0;
-                        ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x + w5 * Pp[0];
+                        ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x + w5 * ppx;
                         ey = w0 * P0[CAPS - 1] + w1 * P0[CAPS + 1] + w2 * P0[CAPS - SW] + w3 * P0[CAPS + SW] +
-                             w4 * m1y + w5 * Pp[CAPS];
+                             w4 * m1y + w5 * ppy;
                         ez = w0 * P0[2 * CAPS - 1] + w1 * P0[2 * CAPS + 1] + w2 * P0[2 * CAPS - SW] +
-                             w3 * P0[2 * CAPS + SW] + w4 * m1z + w5 * Pp[2 * CAPS];
+                             w3 * P0[2 * CAPS + SW] + w4 * m1z + w5 * ppz;
                     }
-                    heun_rhs(a, sx, sy, sz, ex, ey, ez, bax, bay, baz, nthx, nthy, nthz, q, nf1x, nf1y, nf1z);
-                    const float npx = sx + nf1x, npy = sy + nf1y, npz = sz + nf1z;
+                    const float ss = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+                    const float3 u = rhs_u(sx, sy, sz, ss, fmaf(a.cJ, ex, hx), fmaf(a.cJ, ey, hy),
+                                           fmaf(a.cJ, ez, fmaf(a.cK, sz, hz)), a.alpha);
+                    const float fx = q * u.x, fy = q * u.y, fz = q * u.z;
+                    anx = fmaf(0.5f, fx, sx);
+                    any = fmaf(0.5f, fy, sy);
+                    anz = fmaf(0.5f, fz, sz);
+                    const float npx = sx + fx, npy = sy + fy, npz = sz + fz;
                     const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
                     sp = make_float4(npx * inv, npy * inv, npz * inv, __uint_as_float(g0));
                 }
                 sP[SK * CAPS + c] = sp;
             }
             stop = __syncthreads_or(bad) != 0;  // the step's one barrier, and the failure vote
-            // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1), k (SK)
+            // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1) and k (own, sp)
             const int kc = k - 1;
             if (inner && kc >= 0 && kc < nz) {
                 const float4 *Q = sP + SKM1 * CAPS + c;
                 const float4 v = Q[0];
                 if (nonzero3(v.x, v.y, v.z)) {
-                    const float4 l = Q[-1], r = Q[1], d = Q[-SW], u = Q[SW];
-                    const float4 zm = sP[SKM2 * CAPS + c], zp = sP[SK * CAPS + c];
+                    const float4 l = Q[-1], r = Q[1], d = Q[-SW], u4 = Q[SW];
+                    const float4 zm = sP[SKM2 * CAPS + c];
                     float ex, ey, ez;
                     if (!mask) {
-                        ex = ((l.x + r.x) + (d.x + u.x)) + (zm.x + zp.x);
-                        ey = ((l.y + r.y) + (d.y + u.y)) + (zm.y + zp.y);
-                        ez = ((l.z + r.z) + (d.z + u.z)) + (zm.z + zp.z);
+                        ex = ((l.x + r.x) + (d.x + u4.x)) + (zm.x + sp.x);
+                        ey = ((l.y + r.y) + (d.y + u4.y)) + (zm.y + sp.y);
+                        ez = ((l.z + r.z) + (d.z + u4.z)) + (zm.z + sp.z);
                     } else {
                         const unsigned g = __float_as_uint(v.w);
                         const float w0 = __float_as_uint(l.w) == g, w1 = __float_as_uint(r.w) == g,
-                                    w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u.w) == g,
-                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(zp.w) == g;
-                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u.x + w4 * zm.x + w5 * zp.x;
-                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u.y + w4 * zm.y + w5 * zp.y;
-                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u.z + w4 * zm.z + w5 * zp.z;
+                                    w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u4.w) == g,
+                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(sp.w) == g;
+                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u4.x + w4 * zm.x + w5 * sp.x;
+                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u4.y + w4 * zm.y + w5 * sp.y;
+                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u4.z + w4 * zm.z + w5 * sp.z;
                     }
-                    float f2x, f2y, f2z;
-                    heun_rhs(a, v.x, v.y, v.z, ex, ey, ez, bax, bay, baz, thx, thy, thz, q, f2x, f2y, f2z);
-                    float ox = m1x + 0.5f * (f1x + f2x);
-                    float oy = m1y + 0.5f * (f1y + f2y);
-                    float oz = m1z + 0.5f * (f1z + f2z);
+                    // S' is a unit vector: S'.S' = 1 in the damping term
+                    const float3 u = rhs_u(v.x, v.y, v.z, 1.f, fmaf(a.cJ, ex, hmx), fmaf(a.cJ, ey, hmy),
+                                           fmaf(a.cJ, ez, fmaf(a.cK, v.z, hmz)), a.alpha);
+                    const float qh = 0.5f * q;
+                    float ox = fmaf(qh, u.x, amx), oy = fmaf(qh, u.y, amy), oz = fmaf(qh, u.z, amz);
                     const float inv = rsqrtf(ox * ox + oy * oy + oz * oz);
                     ox *= inv;
                     oy *= inv;
@@ -400,13 +405,16 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
             m1x = sx;
             m1y = sy;
             m1z = sz;
+            c0x = ppx;
+            c0y = ppy;
+            c0z = ppz;
             gm1 = g0;
-            f1x = nf1x;
-            f1y = nf1y;
-            f1z = nf1z;
-            thx = nthx;
-            thy = nthy;
-            thz = nthz;
+            amx = anx;
+            amy = any;
+            amz = anz;
+            hmx = hx;
+            hmy = hy;
+            hmz = hz;
         };
 
         // k runs from -1 to nz; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
