@@ -202,14 +202,23 @@ int hamr_load_state(hamr_t h, const char *path);
 /* Launch shape of the fused FP32 stencil kernel: CTA size `threads` and `staged`, the number
  * of positions per plane a CTA stages in shared memory (row pitch x rows).  Each replica is
  * split into column blocks that fit the shape: the block plus a two-column halo within the
- * staged region, and the block plus a one-column halo within `threads`; the split is chosen
- * per replica by a work model.  Compiled (threads, pitch x rows): (1024, 68 x 24),
- * (512, 36 x 24), (256, 36 x 14), (1024, 36 x 40).  hamr_autotune times every compiled shape
- * on the current state (advancing nothing: state and step are restored) and keeps the
- * fastest.  Errors: ARG (shape not compiled), STATE, CUDA. */
+ * staged region, and the block plus a one-column halo within the columns the CTA lists
+ * (one or two per thread); the split is chosen per replica by a work model.  Compiled
+ * (threads, columns per thread, pitch x rows): (512, 1, 36 x 24), (1024, 1, 68 x 24),
+ * (256, 1, 36 x 14), (256, 2, 36 x 24).  hamr_autotune times every compiled shape on the
+ * current state (advancing nothing: state and step are restored) and keeps the fastest.
+ * Errors: ARG (shape not compiled), STATE, CUDA. */
 int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged);
 int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged);
 int hamr_autotune(hamr_t h, int32_t steps_per_trial);
+
+/* Failure-detection test hook (no counterpart in the paper).  The next step call makes the
+ * CTA that takes the first work item of its first step withhold one arrival on the staging
+ * barrier of plane 1, so that its bounded waits run out after `polls` polls (instead of
+ * 2^22).  That call returns HAMR_ERR_TIMEOUT and leaves the spin state invalid (set it
+ * again); the device context stays usable.  Nothing faults.  Fused FP32 stencil handles
+ * only.  Errors: ARG (polls < 1), STATE (other handles). */
+int hamr_inject_wait_timeout(hamr_t h, int32_t polls);
 
 /* Sizes: key 0 = total lattice sites, 1 = magnetic sites, 2 = device bytes held,
  * 3 = kernel launches per step (excluding records), 4 = storage slots. */

@@ -75,7 +75,8 @@ struct WorkItem {
 
 // A compiled variant of the fused kernel.
 struct FusedVariant {
-    int threads;  // CTA size; one listed column per thread
+    int threads;  // CTA size
+    int columns;  // listed columns per work item at most (a whole number per thread)
     int pitch;    // staged-region row pitch: bx + 4 <= pitch
     int rows;     // staged-region rows: by + 4 <= rows
     int staged;   // pitch * rows
@@ -112,6 +113,9 @@ struct FusedArgs {
     int per[3];
     unsigned long long *grain_fx;  // [G][3] fixed-point (2^-24) sums at record steps
     const CUtensorMap *maps;       // [R][2] tensor maps of each replica's state in each buffer
+    unsigned wait_polls;           // a bounded device wait fails after this many polls
+    int inject;                    // failure-detection test: 1 = the CTA of work item 0 withholds
+                                   // one arrival on the staging barrier of plane 1
 };
 
 // kernel launchers (kernels_*.cu)
@@ -205,6 +209,7 @@ struct hamr_ctx {
     CUtensorMap *maps_d = nullptr;    // [R][2] (variant-dependent box)
     std::vector<int> tma_ok;          // replica staged by TMA (open in x and y, no grain mask)
     int fused_grid = 0;
+    unsigned inject_polls = 0;        // >0: the next step block runs the failure test
     bool items_dirty = true;
     int num_sms = 0;
     size_t dev_bytes = 0;

@@ -37,7 +37,7 @@
 namespace hamr {
 
 constexpr int NSLOT = 4;                  // ring depth (planes)
-constexpr unsigned WAIT_LIMIT = 1u << 22;  // polls of an mbarrier before the kernel gives up
+
 
 template <int NT, int SW, int SH>
 struct FusedShape {
@@ -103,9 +103,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
     return ok != 0;
 }
 
-// bounded wait: false when the phase did not complete within WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+// bounded wait: false when the phase did not complete within `polls` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, unsigned polls) {
+    for (unsigned i = 0; i < polls; ++i)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -129,8 +129,8 @@ __device__ __forceinline__ float3 rhs_u(float sx, float sy, float sz, float ss, 
                        fmaf(al, fmaf(sb, sz, -ss * bz), cz));
 }
 
-template <int NT, int SW, int SH, bool RECORD>
-__global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_fused(FusedArgs a) {
+template <int NT, int E, int SW, int SH, int MINB, bool RECORD>
+__global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     using Sh = FusedShape<NT, SW, SH>;
     constexpr int CAPS = Sh::CAPS, LPT = Sh::LPT, SLOT_F = Sh::SLOT_F;
     extern __shared__ unsigned char smem_raw[];
@@ -182,25 +182,33 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
         for (int i = tid; i < NSLOT * CAPS; i += NT) sP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
 
-        // this thread's list entry (site and storage indices fit in 32 bits: a replica has at
-        // most 2^30 sites and the storage fewer than 2^28 slots)
-        const bool act = tid < n_act;
-        bool inner = false;  // interior column: corrected by this thread
-        int c = 0;           // staged-region position
-        float sig = 0.f;     // thermal-field scale of the column
-        unsigned scol = 0;   // site index of the column on plane 0
-        int ocol = 0;        // storage slot of the column on plane 0
-        if (act) {
-            const unsigned e = a.lists[W.list_off + tid];
-            c = (int)(e & 0x7fffu);
-            inner = (e & 0x8000u) != 0;
-            bool ok = true;
-            const int wx = wrap_coord(xs + c % SW, nx, a.per[0], ok);
-            const int wy = wrap_coord(ys + c / SW, ny, a.per[1], ok);
-            const float T = temperature_f(R, (wx + 0.5f) * a.ax, (wy + 0.5f) * a.ay, t);
-            sig = a.sig0 * sqrtf(T);
-            scol = (unsigned)wx + (unsigned)nx * (unsigned)wy;
-            ocol = off + wx + px * wy;
+        // this thread's list entries tid, tid + NT, ... (site and storage indices fit in 32
+        // bits: a replica has at most 2^30 sites and the storage fewer than 2^28 slots)
+        bool act[E], inner[E];  // listed; interior column (corrected by this thread)
+        int c[E];               // staged-region position
+        float sig[E];           // thermal-field scale of the column
+        unsigned scol[E];       // site index of the column on plane 0
+        int ocol[E];            // storage slot of the column on plane 0
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            act[j] = tid + j * NT < n_act;
+            inner[j] = false;
+            c[j] = 0;
+            sig[j] = 0.f;
+            scol[j] = 0;
+            ocol[j] = 0;
+            if (act[j]) {
+                const unsigned e = a.lists[W.list_off + tid + j * NT];
+                c[j] = (int)(e & 0x7fffu);
+                inner[j] = (e & 0x8000u) != 0;
+                bool ok = true;
+                const int wx = wrap_coord(xs + c[j] % SW, nx, a.per[0], ok);
+                const int wy = wrap_coord(ys + c[j] / SW, ny, a.per[1], ok);
+                const float T = temperature_f(R, (wx + 0.5f) * a.ax, (wy + 0.5f) * a.ay, t);
+                sig[j] = a.sig0 * sqrtf(T);
+                scol[j] = (unsigned)wx + (unsigned)nx * (unsigned)wy;
+                ocol[j] = off + wx + px * wy;
+            }
         }
         // per-position copies (fallback): column offsets within a plane (-1: zero-filled,
         // -2: outside the block's staged region)
@@ -218,12 +226,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
             }
         }
         // stage plane p into ring slot p mod 4 (planes beyond nz + 1 are never needed)
-        auto issue = [&](int p) {
+        auto issue = [&](int p, bool withhold = false) {
             if (p > nz + 1) return;
             const int slot = (p + 4) & 3;
             float *dst = sS + slot * SLOT_F;
             bool ok = true;
             const int z = wrap_coord(p, nz, a.per[2], ok);
+            // failure-detection test: the phase of this fill can then never complete
+            if (withhold && tid == 0) return;
             if (tma) {
                 if (tid == 0) {
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
         bool bad = false;
         auto await = [&](int p) {
             const int slot = (p + 4) & 3;
-            if (!mbar_wait(&s_bar[slot], (ph >> slot) & 1u)) {
+            if (!mbar_wait(&s_bar[slot], (ph >> slot) & 1u, a.wait_polls)) {
                 bad = true;
                 atomicOr(&a.ctl->err, 2);
             }
@@ -266,29 +276,37 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
         const float bax = bapp * R.fdir[0], bay = bapp * R.fdir[1], baz = bapp * R.fdir[2];
         const unsigned site_plane = (unsigned)nx * (unsigned)ny;
 
-        // prologue: planes -2 .. 1 staged; own S (and grain code) of plane -2 read
+        // prologue: planes -2 .. 1 staged; own S (and grain code) of planes -2 and -1 read
         issue(-2);
         issue(-1);
         issue(0);
-        issue(1);
+        issue(1, a.inject && it == 0);
         await(-2);
         await(-1);
         await(0);
-        float m1x = 0.f, m1y = 0.f, m1z = 0.f;     // S on plane k-1 at this column
-        float c0x = 0.f, c0y = 0.f, c0z = 0.f;     // S on plane k
-        unsigned gm1 = 0;                           // grain code of plane k-1 (masked replicas)
-        float amx = 0.f, amy = 0.f, amz = 0.f;     // S + dt f(S, B(S)) / 2 of plane k-1
-        float hmx = 0.f, hmy = 0.f, hmz = 0.f;     // B_app + B_th of plane k-1
-        int ax_ = 0, ay_ = 0, az_ = 0, gacc = -1;  // fixed-point record sums of this column
-        if (act) {
-            const float *S2 = sS + 2 * SLOT_F, *S3 = sS + 3 * SLOT_F;  // planes -2 and -1
-            m1x = S2[c];
-            m1y = S2[CAPS + c];
-            m1z = S2[2 * CAPS + c];
-            gm1 = sG[2 * CAPS + c];
-            c0x = S3[c];
-            c0y = S3[CAPS + c];
-            c0z = S3[2 * CAPS + c];
+        float m1x[E], m1y[E], m1z[E];  // S on plane k-1 at each column
+        float c0x[E], c0y[E], c0z[E];  // S on plane k
+        unsigned gm1[E];               // grain code of plane k-1 (masked replicas)
+        float amx[E], amy[E], amz[E];  // S + dt f(S, B(S)) / 2 of plane k-1
+        float hmx[E], hmy[E], hmz[E];  // B_app + B_th of plane k-1
+        int ax_[E], ay_[E], az_[E], gacc[E];  // fixed-point record sums of each column
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            m1x[j] = m1y[j] = m1z[j] = c0x[j] = c0y[j] = c0z[j] = 0.f;
+            amx[j] = amy[j] = amz[j] = hmx[j] = hmy[j] = hmz[j] = 0.f;
+            gm1[j] = 0;
+            ax_[j] = ay_[j] = az_[j] = 0;
+            gacc[j] = -1;
+            if (act[j]) {
+                const float *S2 = sS + 2 * SLOT_F + c[j], *S3 = sS + 3 * SLOT_F + c[j];  // planes -2, -1
+                m1x[j] = S2[0];
+                m1y[j] = S2[CAPS];
+                m1z[j] = S2[2 * CAPS];
+                gm1[j] = sG[2 * CAPS + c[j]];
+                c0x[j] = S3[0];
+                c0y[j] = S3[CAPS];
+                c0z[j] = S3[2 * CAPS];
+            }
         }
         // plane -2's slot is restaged by the first march step; plain grain-code stores become visible
         stop = __syncthreads_or(bad) != 0;
@@ -299,122 +317,139 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
             constexpr int SK = (PH + 3) & 3, SK1 = PH & 3, SKM1 = (PH + 2) & 3, SKM2 = (PH + 1) & 3;
             issue(k + 3);  // into slot (k + 3) mod 4 = SKM1, left by plane k-1 (kept in registers)
             if (k >= 0) await(k + 1);  // plane 0 was awaited by the prologue
-            // ---- predictor on plane k (its own S is in c0, carried from the last step)
             bool zok = true;
             const int wz = wrap_coord(k, nz, a.per[2], zok);
-            const float *P0 = sS + SK * SLOT_F + c, *Pp = sS + SK1 * SLOT_F + c;
-            const float sx = c0x, sy = c0y, sz = c0z;
-            const float ppx = Pp[0], ppy = Pp[CAPS], ppz = Pp[2 * CAPS];
-            unsigned g0 = 0;
-            float anx = 0.f, any = 0.f, anz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-            float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (act) {
-                if (mask) g0 = sG[SK * CAPS + c];
-                const bool mag = mask ? g0 != 0 : nonzero3(sx, sy, sz);
-                if (zok && mag) {
-                    float n0, n1, n2;
-                    normals3(philox10_rk(philox_ctr(scol + site_plane * (unsigned)wz, (unsigned long long)step), s_rk),
-                             n0, n1, n2);
-                    hx = fmaf(sig, n0, bax);
-                    hy = fmaf(sig, n1, bay);
-                    hz = fmaf(sig, n2, baz);
-                    float ex, ey, ez;
-                    if (!mask) {
-                        ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x + ppx);
-                        ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y + ppy);
-                        ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
-                             (m1z + ppz);
-                    } else {
-                        const uint16_t *G0 = sG + SK * CAPS + c;
-                        const float w0 = G0[-1] == g0, w1 = G0[1] == g0, w2 = G0[-SW] == g0, w3 = G0[SW] == g0,
-                                    w4 = gm1 == g0, w5 = sG[SK1 * CAPS + c] == g0;
-                        ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x + w5 * ppx;
-                        ey = w0 * P0[CAPS - 1] + w1 * P0[CAPS + 1] + w2 * P0[CAPS - SW] + w3 * P0[CAPS + SW] +
-                             w4 * m1y + w5 * ppy;
-                        ez = w0 * P0[2 * CAPS - 1] + w1 * P0[2 * CAPS + 1] + w2 * P0[2 * CAPS - SW] +
-                             w3 * P0[2 * CAPS + SW] + w4 * m1z + w5 * ppz;
+            float4 sp[E];       // S' of plane k (own, for the corrector's z+ neighbour)
+            float ppx[E], ppy[E], ppz[E];
+            unsigned g0[E];
+            float anx[E], any[E], anz[E], hx[E], hy[E], hz[E];
+            // ---- predictor on plane k (each column's own S is in c0, carried from the last step)
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const float *P0 = sS + SK * SLOT_F + c[j], *Pp = sS + SK1 * SLOT_F + c[j];
+                const float sx = c0x[j], sy = c0y[j], sz = c0z[j];
+                ppx[j] = Pp[0];
+                ppy[j] = Pp[CAPS];
+                ppz[j] = Pp[2 * CAPS];
+                g0[j] = 0;
+                anx[j] = any[j] = anz[j] = hx[j] = hy[j] = hz[j] = 0.f;
+                sp[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (act[j]) {
+                    if (mask) g0[j] = sG[SK * CAPS + c[j]];
+                    const bool mag = mask ? g0[j] != 0 : nonzero3(sx, sy, sz);
+                    if (zok && mag) {
+                        float n0, n1, n2;
+                        normals3(philox10_rk(philox_ctr(scol[j] + site_plane * (unsigned)wz, (unsigned long long)step),
+                                             s_rk),
+                                 n0, n1, n2);
+                        hx[j] = fmaf(sig[j], n0, bax);
+                        hy[j] = fmaf(sig[j], n1, bay);
+                        hz[j] = fmaf(sig[j], n2, baz);
+                        float ex, ey, ez;
+                        if (!mask) {
+                            ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x[j] + ppx[j]);
+                            ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y[j] + ppy[j]);
+                            ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
+                                 (m1z[j] + ppz[j]);
+                        } else {
+                            const uint16_t *G0 = sG + SK * CAPS + c[j];
+                            const unsigned g = g0[j];
+                            const float w0 = G0[-1] == g, w1 = G0[1] == g, w2 = G0[-SW] == g, w3 = G0[SW] == g,
+                                        w4 = gm1[j] == g, w5 = sG[SK1 * CAPS + c[j]] == g;
+                            ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x[j] + w5 * ppx[j];
+                            ey = w0 * P0[CAPS - 1] + w1 * P0[CAPS + 1] + w2 * P0[CAPS - SW] + w3 * P0[CAPS + SW] +
+                                 w4 * m1y[j] + w5 * ppy[j];
+                            ez = w0 * P0[2 * CAPS - 1] + w1 * P0[2 * CAPS + 1] + w2 * P0[2 * CAPS - SW] +
+                                 w3 * P0[2 * CAPS + SW] + w4 * m1z[j] + w5 * ppz[j];
+                        }
+                        const float ss = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+                        const float3 u = rhs_u(sx, sy, sz, ss, fmaf(a.cJ, ex, hx[j]), fmaf(a.cJ, ey, hy[j]),
+                                               fmaf(a.cJ, ez, fmaf(a.cK, sz, hz[j])), a.alpha);
+                        const float fx = q * u.x, fy = q * u.y, fz = q * u.z;
+                        anx[j] = fmaf(0.5f, fx, sx);
+                        any[j] = fmaf(0.5f, fy, sy);
+                        anz[j] = fmaf(0.5f, fz, sz);
+                        const float npx = sx + fx, npy = sy + fy, npz = sz + fz;
+                        const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
+                        sp[j] = make_float4(npx * inv, npy * inv, npz * inv, __uint_as_float(g0[j]));
                     }
-                    const float ss = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
-                    const float3 u = rhs_u(sx, sy, sz, ss, fmaf(a.cJ, ex, hx), fmaf(a.cJ, ey, hy),
-                                           fmaf(a.cJ, ez, fmaf(a.cK, sz, hz)), a.alpha);
-                    const float fx = q * u.x, fy = q * u.y, fz = q * u.z;
-                    anx = fmaf(0.5f, fx, sx);
-                    any = fmaf(0.5f, fy, sy);
-                    anz = fmaf(0.5f, fz, sz);
-                    const float npx = sx + fx, npy = sy + fy, npz = sz + fz;
-                    const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
-                    sp = make_float4(npx * inv, npy * inv, npz * inv, __uint_as_float(g0));
+                    sP[SK * CAPS + c[j]] = sp[j];
                 }
-                sP[SK * CAPS + c] = sp;
             }
             stop = __syncthreads_or(bad) != 0;  // the step's one barrier, and the failure vote
             // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1) and k (own, sp)
             const int kc = k - 1;
-            if (inner && kc >= 0 && kc < nz) {
-                const float4 *Q = sP + SKM1 * CAPS + c;
-                const float4 v = Q[0];
-                if (nonzero3(v.x, v.y, v.z)) {
+            if (kc >= 0 && kc < nz) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    if (!inner[j]) continue;
+                    const float4 *Q = sP + SKM1 * CAPS + c[j];
+                    const float4 v = Q[0];
+                    if (!nonzero3(v.x, v.y, v.z)) continue;
                     const float4 l = Q[-1], r = Q[1], d = Q[-SW], u4 = Q[SW];
-                    const float4 zm = sP[SKM2 * CAPS + c];
+                    const float4 zm = sP[SKM2 * CAPS + c[j]], zp = sp[j];
                     float ex, ey, ez;
                     if (!mask) {
-                        ex = ((l.x + r.x) + (d.x + u4.x)) + (zm.x + sp.x);
-                        ey = ((l.y + r.y) + (d.y + u4.y)) + (zm.y + sp.y);
-                        ez = ((l.z + r.z) + (d.z + u4.z)) + (zm.z + sp.z);
+                        ex = ((l.x + r.x) + (d.x + u4.x)) + (zm.x + zp.x);
+                        ey = ((l.y + r.y) + (d.y + u4.y)) + (zm.y + zp.y);
+                        ez = ((l.z + r.z) + (d.z + u4.z)) + (zm.z + zp.z);
                     } else {
                         const unsigned g = __float_as_uint(v.w);
                         const float w0 = __float_as_uint(l.w) == g, w1 = __float_as_uint(r.w) == g,
                                     w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u4.w) == g,
-                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(sp.w) == g;
-                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u4.x + w4 * zm.x + w5 * sp.x;
-                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u4.y + w4 * zm.y + w5 * sp.y;
-                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u4.z + w4 * zm.z + w5 * sp.z;
+                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(zp.w) == g;
+                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u4.x + w4 * zm.x + w5 * zp.x;
+                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u4.y + w4 * zm.y + w5 * zp.y;
+                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u4.z + w4 * zm.z + w5 * zp.z;
                     }
                     // S' is a unit vector: S'.S' = 1 in the damping term
-                    const float3 u = rhs_u(v.x, v.y, v.z, 1.f, fmaf(a.cJ, ex, hmx), fmaf(a.cJ, ey, hmy),
-                                           fmaf(a.cJ, ez, fmaf(a.cK, v.z, hmz)), a.alpha);
+                    const float3 u = rhs_u(v.x, v.y, v.z, 1.f, fmaf(a.cJ, ex, hmx[j]), fmaf(a.cJ, ey, hmy[j]),
+                                           fmaf(a.cJ, ez, fmaf(a.cK, v.z, hmz[j])), a.alpha);
                     const float qh = 0.5f * q;
-                    float ox = fmaf(qh, u.x, amx), oy = fmaf(qh, u.y, amy), oz = fmaf(qh, u.z, amz);
+                    float ox = fmaf(qh, u.x, amx[j]), oy = fmaf(qh, u.y, amy[j]), oz = fmaf(qh, u.z, amz[j]);
                     const float inv = rsqrtf(ox * ox + oy * oy + oz * oz);
                     ox *= inv;
                     oy *= inv;
                     oz *= inv;
-                    const int o = ocol + kc * plane;
+                    const int o = ocol[j] + kc * plane;
                     Sout[o] = ox;
                     Sout[NS + o] = oy;
                     Sout[2 * NS + o] = oz;
                     if (RECORD) {
                         const unsigned g = mask ? __float_as_uint(v.w) : (unsigned)__ldg(a.gcode + o);
                         const int gg = R.grain_off + (int)g - 1;
-                        if (gg != gacc || (kc & 63) == 63) {
-                            if (gacc >= 0) {
-                                atomicAdd(a.grain_fx + 3 * gacc + 0, (unsigned long long)(long long)ax_);
-                                atomicAdd(a.grain_fx + 3 * gacc + 1, (unsigned long long)(long long)ay_);
-                                atomicAdd(a.grain_fx + 3 * gacc + 2, (unsigned long long)(long long)az_);
+                        if (gg != gacc[j] || (kc & 63) == 63) {
+                            if (gacc[j] >= 0) {
+                                atomicAdd(a.grain_fx + 3 * gacc[j] + 0, (unsigned long long)(long long)ax_[j]);
+                                atomicAdd(a.grain_fx + 3 * gacc[j] + 1, (unsigned long long)(long long)ay_[j]);
+                                atomicAdd(a.grain_fx + 3 * gacc[j] + 2, (unsigned long long)(long long)az_[j]);
                             }
-                            gacc = gg;
-                            ax_ = ay_ = az_ = 0;
+                            gacc[j] = gg;
+                            ax_[j] = ay_[j] = az_[j] = 0;
                         }
-                        ax_ += __float2int_rn(ox * FX_SCALE);
-                        ay_ += __float2int_rn(oy * FX_SCALE);
-                        az_ += __float2int_rn(oz * FX_SCALE);
+                        ax_[j] += __float2int_rn(ox * FX_SCALE);
+                        ay_[j] += __float2int_rn(oy * FX_SCALE);
+                        az_[j] += __float2int_rn(oz * FX_SCALE);
                     }
                 }
             }
-            // carry this column's plane-k values to the next march step
-            m1x = sx;
-            m1y = sy;
-            m1z = sz;
-            c0x = ppx;
-            c0y = ppy;
-            c0z = ppz;
-            gm1 = g0;
-            amx = anx;
-            amy = any;
-            amz = anz;
-            hmx = hx;
-            hmy = hy;
-            hmz = hz;
+            // carry each column's plane-k values to the next march step
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                m1x[j] = c0x[j];
+                m1y[j] = c0y[j];
+                m1z[j] = c0z[j];
+                c0x[j] = ppx[j];
+                c0y[j] = ppy[j];
+                c0z[j] = ppz[j];
+                gm1[j] = g0[j];
+                amx[j] = anx[j];
+                amy[j] = any[j];
+                amz[j] = anz[j];
+                hmx[j] = hx[j];
+                hmy[j] = hy[j];
+                hmz[j] = hz[j];
+            }
         };
 
         // k runs from -1 to nz; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
@@ -430,25 +465,32 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) k_
             // give the fills issued after the last awaited plane a bounded time to land before
             // the CTA's shared memory is released
             if (tid == 0)
-                for (int p = max(kend + 2, 1); p <= min(kend + 3, nz + 1); ++p) await(p);
+                for (int p = max(kend + 2, 1); p <= min(kend + 3, nz + 1); ++p) {
+                    const int slot = (p + 4) & 3;
+                    mbar_wait(&s_bar[slot], (ph >> slot) & 1u, 1u << 22);
+                    ph ^= 1u << slot;
+                }
             return;  // uniform: every thread saw the same vote
         }
-        if (RECORD) grain_accumulate_fx(a.grain_fx, gacc, ax_, ay_, az_, gacc >= 0);
+        if (RECORD) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) grain_accumulate_fx(a.grain_fx, gacc[j], ax_[j], ay_[j], az_[j], gacc[j] >= 0);
+        }
         __syncthreads();  // all reads of this item's slots are done before they are re-armed
     }
 }
 
 // Opt in to the variant's dynamic shared memory (done before any stream capture, when the
 // work list is built).
-template <int NT, int SW, int SH>
+template <int NT, int E, int SW, int SH, int MINB>
 static cudaError_t ensure_attrs() {
     using Sh = FusedShape<NT, SW, SH>;
     static bool init = false;
     if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<NT, SW, SH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Sh::smem);
+        cudaError_t e = cudaFuncSetAttribute(k_fused<NT, E, SW, SH, MINB, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused<NT, SW, SH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_fused<NT, E, SW, SH, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Sh::smem);
         if (e != cudaSuccess) return e;
         init = true;
@@ -456,50 +498,54 @@ static cudaError_t ensure_attrs() {
     return cudaSuccess;
 }
 
-template <int NT, int SW, int SH>
+template <int NT, int E, int SW, int SH, int MINB>
 static cudaError_t launch_variant(const FusedArgs &a, int grid, bool record, cudaStream_t st) {
     using Sh = FusedShape<NT, SW, SH>;
-    cudaError_t e = ensure_attrs<NT, SW, SH>();
+    cudaError_t e = ensure_attrs<NT, E, SW, SH, MINB>();
     if (e != cudaSuccess) return e;
     if (record)
-        k_fused<NT, SW, SH, true><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<NT, E, SW, SH, MINB, true><<<grid, NT, Sh::smem, st>>>(a);
     else
-        k_fused<NT, SW, SH, false><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<NT, E, SW, SH, MINB, false><<<grid, NT, Sh::smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NT, int SW, int SH>
+template <int NT, int E, int SW, int SH, int MINB>
 static int blocks_per_sm() {
     using Sh = FusedShape<NT, SW, SH>;
     int n = 0;
-    if (ensure_attrs<NT, SW, SH>() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<NT, SW, SH, false>, NT, Sh::smem) != cudaSuccess)
+    if (ensure_attrs<NT, E, SW, SH, MINB>() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<NT, E, SW, SH, MINB, false>, NT, Sh::smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
 
-// compiled variants: threads per CTA and the staged region's pitch x rows (pitch a multiple
-// of 4 so that TMA rows are 16-byte multiples).  A block of bx x by columns fits when
-// bx + 4 <= pitch (bx + 7 with TMA, whose origin is rounded down to a multiple of 4),
-// by + 4 <= rows and it lists at most one column per thread.
-#define HAMR_FUSED_VARIANTS(X) X(0, 1024, 68, 24) X(1, 512, 36, 24) X(2, 256, 36, 14) X(3, 1024, 36, 40)
+// compiled variants: threads per CTA, listed columns per thread, the staged region's pitch x
+// rows (pitch a multiple of 4 so that TMA rows are 16-byte multiples) and the CTAs per SM the
+// register budget is sized for.  A block of bx x by columns fits when bx + 4 <= pitch (bx + 7
+// with TMA, whose origin is rounded down to a multiple of 4), by + 4 <= rows and it lists at
+// most threads x columns-per-thread columns.
+#define HAMR_FUSED_VARIANTS(X) \
+    X(0, 512, 1, 36, 24, 2) X(1, 1024, 1, 68, 24, 1) X(2, 256, 1, 36, 14, 3) X(3, 256, 2, 36, 24, 2)
 
 cudaError_t launch_fused_step(int v, const FusedArgs &a, int grid, bool record, cudaStream_t st) {
-#define X(I, NT, SW, SH) \
-    if (v == I) return launch_variant<NT, SW, SH>(a, grid, record, st);
+#define X(I, NT, E, SW, SH, MINB) \
+    if (v == I) return launch_variant<NT, E, SW, SH, MINB>(a, grid, record, st);
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
 bool fused_variant(int v, FusedVariant &out) {
-#define X(I, NT, SW, SH)      \
-    if (v == I) {             \
-        out.threads = NT;     \
-        out.pitch = SW;       \
-        out.rows = SH;        \
-        out.staged = SW * SH; \
-        return true;          \
+#define X(I, NT, E, SW, SH, MINB) \
+    if (v == I) {                 \
+        out.threads = NT;         \
+        out.columns = NT * E;     \
+        out.pitch = SW;           \
+        out.rows = SH;            \
+        out.staged = SW * SH;     \
+        return true;              \
     }
     HAMR_FUSED_VARIANTS(X)
 #undef X
@@ -507,8 +553,8 @@ bool fused_variant(int v, FusedVariant &out) {
 }
 
 int fused_max_blocks_per_sm(int v) {
-#define X(I, NT, SW, SH) \
-    if (v == I) return blocks_per_sm<NT, SW, SH>();
+#define X(I, NT, E, SW, SH, MINB) \
+    if (v == I) return blocks_per_sm<NT, E, SW, SH, MINB>();
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return 0;

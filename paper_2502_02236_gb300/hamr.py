@@ -26,7 +26,7 @@ EXPORTS = [
     "hamr_read_magnetisation", "hamr_clear_records", "hamr_read_energy", "hamr_get_step",
     "hamr_set_step", "hamr_check_finite", "hamr_save_state", "hamr_load_state", "hamr_set_tile",
     "hamr_get_tile", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
-    "hamr_sllg_heun_step_noalloc",
+    "hamr_sllg_heun_step_noalloc", "hamr_inject_wait_timeout",
 ]
 NOALLOC_MAX_SITES = 131072
 
@@ -102,6 +102,7 @@ def lib():
             "hamr_autotune": [vp, i32],
             "hamr_query": [vp, i32, vp],
             "hamr_sllg_heun_step_noalloc": [vp, vp, vp, vp, i64, vp],
+            "hamr_inject_wait_timeout": [vp, i32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -314,6 +315,11 @@ class Lattice:
     def autotune(self, steps_per_trial=20):
         self._ck(lib().hamr_autotune(self._h, int(steps_per_trial)))
         return self.get_tile()
+
+    def inject_wait_timeout(self, polls):
+        """Failure-detection test: the next step call has one bounded device wait run out
+        after `polls` polls and raises HamrError with code ERR_TIMEOUT."""
+        self._ck(lib().hamr_inject_wait_timeout(self._h, int(polls)))
 
     def query(self, key):
         v = ctypes.c_int64()

@@ -116,7 +116,7 @@ def test_fp32_sc32_pbc_thermal_1000():
     assert max_abs(Mg, Mo) < TOL32
 
 
-TILES = [(1024, 68 * 24), (512, 36 * 24), (256, 36 * 14), (1024, 36 * 40)]
+TILES = [(512, 36 * 24), (1024, 68 * 24), (256, 36 * 14), (256, 36 * 24)]
 
 
 @pytest.mark.parametrize("tile", TILES)

@@ -1,0 +1,73 @@
+"""Per-grain thermal switching probability: FP32 batched GPU runs against the FP64 oracle on
+the same seeds, compared within the binomial error of the two proportions.
+
+128 replicas of a 17 x 17 x 4 simple-cubic block cut into four columnar grains by a
+one-site non-magnetic cross (512 grains of 256 sites), all starting along +z at 600 K under
+2 T along -z with alpha = 1 and dt = 0.5 fs, 2000 Heun steps.  A grain has switched when its
+mean S_z is negative at the end; about a third of the grains switch.  The FP32 and FP64
+trajectories share their thermal noise but separate through rounding, so outcomes agree
+only statistically.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+R, NX, NZ, STEPS, T, B0, DT, ALPHA = 128, 17, 4, 2000, 600.0, 2.0, 0.5e-15, 1.0
+
+
+def grain_map():
+    g = np.full((NZ, NX, NX), -1, dtype=np.int32)
+    h = NX // 2
+    for y in range(NX):
+        for x in range(NX):
+            if x != h and y != h:
+                g[:, y, x] = (1 if x > h else 0) + (2 if y > h else 0)
+    return g.reshape(-1)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_02236_gb300 import build
+    build.build()
+    from paper_2502_02236_gb300 import hamr, inputs as I
+    return hamr, I
+
+
+def test_per_grain_switching_probability_matches_oracle(env):
+    hamr, I = env
+    import oracle as orc
+    g = grain_map()
+    n = g.size
+    seeds = [1000 + r for r in range(R)]
+    with hamr.Lattice([(NX, NX, NZ)] * R, seeds, precision="fp32", a=0.25e-9, mu_s=I.MU_S, ku=I.KU_SC,
+                      alpha=ALPHA, dt=DT) as lat:
+        lat.set_neighbour_shells([I.J_SC])
+        for r in range(R):
+            lat.set_grain_map(r, g, 4)
+            lat.set_temperature_profile(r, T)
+            lat.set_field_sequence(r, B0, (0, 0, -1))
+        lat.sllg_heun_steps(STEPS, STEPS)
+        mz_gpu = np.array([lat.read_magnetisation(r, n_grains=4)[2][:, 2] for r in range(R)])
+    mz_orc = []
+    for r in range(R):
+        p = orc.sc_params(NX, NX, NZ, 0.25e-9, I.J_SC, ku=I.KU_SC, mu_s=I.MU_S, alpha=ALPHA, dt=DT, T_amb=T,
+                          B0=B0, direction=(0, 0, -1), seed=seeds[r])
+        o = orc.Oracle(p, g)
+        S = I.mask_void(I.initial_state(n, "+z"), g)
+        o.run(S, 0, STEPS)
+        sums, cnt = o.grain_sums(S, 4)
+        mz_orc.append(sums[:, 2] / cnt)
+    mz_orc = np.array(mz_orc)
+    p_gpu, p_orc = (mz_gpu < 0).mean(), (mz_orc < 0).mean()
+    N = mz_gpu.size
+    p = 0.5 * (p_gpu + p_orc)
+    sigma = math.sqrt(max(p * (1 - p), 1e-4) * 2 / N)
+    print("switching probability GPU FP32 %.3f, oracle FP64 %.3f (%d grains, sigma %.3f)" % (p_gpu, p_orc, N, sigma))
+    assert 0.1 < p_orc < 0.9, p_orc           # the workload does switch some grains, not all
+    assert abs(p_gpu - p_orc) < 3 * sigma, (p_gpu, p_orc, sigma)
