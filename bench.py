@@ -154,17 +154,24 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources_sha256():
+    """Hash of the fused kernel's sources (the template, its simple-cubic instantiation and
+    the device helpers it includes)."""
+    h = hashlib.sha256()
+    for f in ("kernels_fused.cuh", "kernels_fused_sc.cu", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2502_02236_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def kernel_traffic():
     """DRAM bytes per fused launch from the committed ncu summary, if it was taken on the
-    kernel source as it is now (else None)."""
-    src = os.path.join(ROOT, "paper_2502_02236_gb300", "csrc", "kernels_fused.cu")
+    kernel sources as they are now (else None)."""
     path = os.path.join(ROOT, "profiles", "fused_ensemble256_traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
-        if t.get("kernel_sha256") == h:
+        if t.get("kernel_sha256") == kernel_sources_sha256():
             return t.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass

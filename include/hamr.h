@@ -74,9 +74,11 @@ typedef struct {
                              ((i+1/2)a/sqrt2, (j+1/2)a/sqrt2, (k+1/2)c) (Appendix A). */
     int32_t precision;    /* HAMR_FP32: spin state and field arithmetic in FP32, FP64
                              reductions.  HAMR_FP64: everything in FP64. */
-    int32_t neighbours;   /* HAMR_NBR_STENCIL: implicit 6-neighbour stencil (SC only).
-                             HAMR_NBR_CSR: neighbour list, built from the geometry at
-                             creation or replaced per replica by hamr_set_csr. */
+    int32_t neighbours;   /* HAMR_NBR_STENCIL: the lattice's implicit stencil (SC: 6
+                             nearest neighbours; L1_0: 4 in-plane nearest, 2 out of plane,
+                             4 in-plane diagonals); FP32 stencil handles run the fused
+                             kernel.  HAMR_NBR_CSR: neighbour list, built from the geometry
+                             at creation or replaced per replica by hamr_set_csr. */
     int32_t n_replicas;   /* independent lattices advanced together, >= 1 */
     const int32_t *dims;  /* [3 * n_replicas]: nx, ny, nz of each replica, each >= 1 */
     const uint64_t *seeds;/* [n_replicas]: Philox key of each replica */
@@ -199,7 +201,8 @@ int hamr_check_finite(hamr_t h);
 int hamr_save_state(hamr_t h, const char *path);
 int hamr_load_state(hamr_t h, const char *path);
 
-/* Launch shape of the fused FP32 stencil kernel: CTA size `threads` and `staged`, the number
+/* Launch shape of the fused FP32 stencil kernel (both lattices): CTA size `threads` and
+ * `staged`, the number
  * of positions per plane a CTA stages in shared memory (row pitch x rows).  Each replica is
  * split into column blocks that fit the shape: the block plus a two-column halo within the
  * staged region, and the block plus a one-column halo within the columns the CTA lists

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhamr.so")
-SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused.cu", "kernels_misc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused_sc.cu", "kernels_fused_l10.cu", "kernels_misc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,7 +46,10 @@ def build(force=False, verbose=False, extra=()):
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, src.replace(".cu", ".o"))
         if force or extra or _stale(o, [s, *headers]):
-            jobs.append([nvcc(), *flags(), *extra, "-c", s, "-o", o])
+            # the fused kernels write every multiply-add out (identical rounding in every
+            # instantiation, see kernels_fused.cuh)
+            fmad = ["-fmad=false"] if src.startswith("kernels_fused") else []
+            jobs.append([nvcc(), *flags(), *fmad, *extra, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

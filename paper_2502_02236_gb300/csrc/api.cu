@@ -70,9 +70,10 @@ void dfree(T *&p) {
 
 size_t elt(const hamr_t h) { return h->prec == HAMR_FP64 ? 8 : 4; }
 
-bool fused_mode(const hamr_t h) {
-    return h->prec == HAMR_FP32 && h->lattice == HAMR_LATTICE_SC && h->nbr == HAMR_NBR_STENCIL;
-}
+// FP32 handles on the implicit stencil (simple cubic or L1_0) run the fused kernel
+bool fused_mode(const hamr_t h) { return h->prec == HAMR_FP32 && h->nbr == HAMR_NBR_STENCIL; }
+
+bool tetragonal(const hamr_t h) { return h->lattice == HAMR_LATTICE_L10; }
 
 void clear_graphs(hamr_t h) {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -476,7 +477,7 @@ int build_items(hamr_t h) {
                           h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->n_items = (int)sorted.size();
-    const int bps = std::max(1, fused_max_blocks_per_sm(h->variant));
+    const int bps = std::max(1, fused_max_blocks_per_sm(h->variant, tetragonal(h)));
     h->fused_grid = std::max(1, std::min(h->n_items, bps * h->num_sms));
     h->items_dirty = false;
     clear_graphs(h);
@@ -496,7 +497,7 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.lists = h->lists_d;
         a.n_items = h->n_items;
         a.ctl = h->ctl_d;
-        a.cJ = (float)h->ph.cJ[0];
+        for (int s = 0; s < 3; ++s) a.cJ[s] = (float)h->ph.cJ[s];
         a.cK = (float)h->ph.cK;
         a.pref = (float)h->ph.pref;
         a.alpha = (float)h->ph.alpha;
@@ -514,7 +515,7 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.Sbuf1 = (float *)h->S[1];
         for (int i = 0; i < G; ++i) {
             a.step_off = i;
-            CK(h, launch_fused_step(h->variant, a, h->fused_grid, record && i == G - 1, h->stream));
+            CK(h, launch_fused_step(h->variant, tetragonal(h), a, h->fused_grid, record && i == G - 1, h->stream));
         }
     } else {
         const int nb = (int)(h->NS / PLAIN_BLOCK);
@@ -766,8 +767,6 @@ int hamr_lattice_create(hamr_t *out, const hamr_lattice_desc *d) {
         return fail(nullptr, HAMR_ERR_ARG, "unknown precision %d", d->precision);
     if (d->neighbours != HAMR_NBR_STENCIL && d->neighbours != HAMR_NBR_CSR)
         return fail(nullptr, HAMR_ERR_ARG, "unknown neighbour mode %d", d->neighbours);
-    if (d->neighbours == HAMR_NBR_STENCIL && d->lattice != HAMR_LATTICE_SC)
-        return fail(nullptr, HAMR_ERR_ARG, "the implicit stencil is for simple-cubic lattices only");
     if (d->n_replicas < 1 || !d->dims || !d->seeds) return fail(nullptr, HAMR_ERR_ARG, "bad replica description");
     if (!(d->a > 0) || (d->lattice == HAMR_LATTICE_L10 && !(d->c > 0)) || !(d->mu_s > 0) || !(d->dt > 0) ||
         !(d->gamma > 0) || !(d->alpha >= 0) || !isfinite(d->ku))
@@ -829,6 +828,7 @@ int hamr_lattice_create(hamr_t *out, const hamr_lattice_desc *d) {
         ph.az = h->c;
     }
     for (int k = 0; k < 3; ++k) ph.per[k] = h->per[k];
+    ph.lattice = h->lattice;
 
     // layout
     h->NS = NS;
@@ -966,7 +966,7 @@ int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t 
             for (long long x = 0; x < R.nx && !cross; ++x) {
                 const uint16_t g = h->gcode_h[slot_of(R, x, y, z)];
                 if (!g) continue;
-                for (const Off &o : bond_offsets(HAMR_LATTICE_SC)) {
+                for (const Off &o : bond_offsets(h->lattice)) {
                     int jx = (int)x + o.dx, jy = (int)y + o.dy, jz = (int)z + o.dz;
                     if (!wrap(jx, R.nx, h->per[0]) || !wrap(jy, R.ny, h->per[1]) || !wrap(jz, R.nz, h->per[2]))
                         continue;
@@ -1262,7 +1262,7 @@ int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged) {
     if (v < 0) return fail(h, HAMR_ERR_ARG, "no compiled kernel variant with %d threads, %d staged positions", threads,
                            staged);
     DeviceGuard dg(h->device);
-    if (fused_max_blocks_per_sm(v) < 1) return fail(h, HAMR_ERR_ARG, "variant %d cannot launch", v);
+    if (fused_max_blocks_per_sm(v, tetragonal(h)) < 1) return fail(h, HAMR_ERR_ARG, "variant %d cannot launch", v);
     if (v != h->variant) {
         h->variant = v;
         h->items_dirty = true;
@@ -1300,7 +1300,7 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     int rc = HAMR_OK;
     FusedVariant v;
     for (int i = 0; fused_variant(i, v); ++i) {
-        if (fused_max_blocks_per_sm(i) < 1) continue;
+        if (fused_max_blocks_per_sm(i, tetragonal(h)) < 1) continue;
         if ((rc = hamr_set_tile(h, v.threads, v.staged))) break;
         if ((rc = steps_impl(h, steps_per_trial, 0, true))) break;  // warm-up, graph capture
         CK(h, cudaEventRecord(e0, h->stream));

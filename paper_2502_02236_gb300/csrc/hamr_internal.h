@@ -51,6 +51,7 @@ struct Phys {
     double ax, ay, az;      // site spacing [m]
     int per[3];
     int n_shells;
+    int lattice;            // HAMR_LATTICE_SC or HAMR_LATTICE_L10 (the implicit stencil's shape)
 };
 
 // Device control block.
@@ -109,7 +110,8 @@ struct FusedArgs {
     int n_items;
     Ctl *ctl;
     int step_off;
-    float cJ, cK, pref, alpha, dt, sig0, ax, ay, az;
+    float cJ[3];                // J_s / mu_s of the stencil's shells (SC: shell 0 only) [T]
+    float cK, pref, alpha, dt, sig0, ax, ay, az;
     int per[3];
     unsigned long long *grain_fx;  // [G][3] fixed-point (2^-24) sums at record steps
     const CUtensorMap *maps;       // [R][2] tensor maps of each replica's state in each buffer
@@ -120,9 +122,10 @@ struct FusedArgs {
 
 // kernel launchers (kernels_*.cu)
 cudaError_t launch_plain_step(int prec, const void *args, int n_blocks, bool record, cudaStream_t st);
-cudaError_t launch_fused_step(int variant, const FusedArgs &a, int grid, bool record, cudaStream_t st);
+// tet: the L1_0 (tetragonal three-shell) stencil instead of the simple-cubic one
+cudaError_t launch_fused_step(int variant, bool tet, const FusedArgs &a, int grid, bool record, cudaStream_t st);
 bool fused_variant(int variant, FusedVariant &out);
-int fused_max_blocks_per_sm(int variant);
+int fused_max_blocks_per_sm(int variant, bool tet);
 cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps,
                                const long long *nmag, const long long *gcount, int Gtot, double *grain_acc,
                                unsigned long long *grain_fx, double *grain_last, double *rec, long long rec_cap,

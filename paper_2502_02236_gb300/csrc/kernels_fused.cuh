@@ -1,5 +1,9 @@
-// Fused FP32 sLLG Heun step for simple-cubic lattices: both Heun stages of a step in one
-// pass over the spin state, for many replicas of uneven size in one persistent launch.
+// Fused FP32 sLLG Heun step for the stencil lattices: both Heun stages of a step in one pass
+// over the spin state, for many replicas of uneven size in one persistent launch.  The
+// simple-cubic lattice has 6 nearest neighbours (one exchange shell); the L1_0 Fe sublattice
+// (square nets of spacing a/sqrt2 stacked at c) has 4 in-plane nearest neighbours, 2 out of
+// plane and 4 in-plane diagonals (three shells).  Both are stencils over the same staged
+// planes: the diagonals are the corners of the halo that the nearest neighbours need anyway.
 //
 // Work item = a block of bx x by columns of one replica spanning all nz planes.  The CTA
 // stages, plane by plane, the spins of the block plus a two-column halo in shared memory and
@@ -11,20 +15,21 @@
 //   1. starts staging plane k+3 into the slot that plane k-1 has left;
 //   2. waits for plane k+1;
 //   3. predicts S' on plane k for every listed column: the block's interior and its
-//      one-column halo, so the corrector never needs another CTA's S';
+//      one-column halo (corners included), so the corrector never needs another CTA's S';
 //   4. synchronises once;
-//   5. corrects plane k-1 on the interior columns from the S' planes k-2, k-1, k.
+//   5. corrects plane k-1 on the interior columns from the S' planes k-2, k-1 (shared
+//      memory) and k (the thread's own, in registers).
 // With four S and four S' slots no other barrier is needed: the next step's writes go to
 // slots that no thread can still be reading.  The four slot mbarriers are initialised once
 // per kernel and keep running phases across work items.
 // The list of columns is built on the host per work item: only columns inside the lattice
 // that hold a magnetic site are listed, so lanes are not spent on the non-magnetic grain
 // boundaries or on halos beyond an open edge; interior columns come first, flagged in the
-// list entry.  Each thread owns one list
-// entry for the whole march and keeps in registers what the next stage needs from its own
-// column: S of the previous plane, dt f(S, B(S)) and the thermal field of the plane awaiting
-// correction.  The march is unrolled over the ring period so that ring slots and neighbour
-// offsets are compile-time constants.
+// list entry.  Each thread owns one list entry (or E of them) for the whole march and keeps
+// in registers what the next stage needs from its own column: S of planes k-1 and k, the
+// corrector base S + dt f(S, B(S)) / 2 and the field terms that do not depend on S (applied
+// plus thermal) of the plane awaiting correction.  The march is unrolled over the ring
+// period so that ring slots and neighbour offsets are compile-time constants.
 // Each site's thermal normals come from its own (replica key, site, step) Philox counter, so
 // halo sites computed by two CTAs get the same noise.  Open edges and non-magnetic sites read
 // as S = 0 (the state of such sites is kept at 0): a zero spin marks a non-magnetic site and
@@ -32,6 +37,8 @@
 // per-grain sums) and for replicas whose grains touch (the exchange mask).
 // Per step the kernel reads S once (12 B/site) and writes S once (12 B/site); halo columns
 // are re-read from L2.
+#pragma once
+
 #include "device_common.cuh"
 
 namespace hamr {
@@ -120,16 +127,117 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// f(S, B) / (dt pref) = S x B + alpha [(S.B) S - (S.S) B]  (Eq. 1 in Landau-Lifshitz form)
+// f(S, B) / (dt pref) = S x B + alpha [(S.B) S - (S.S) B]  (Eq. 1 in Landau-Lifshitz form).
+// The fused kernels are compiled without implicit multiply-add contraction, and every fused
+// multiply-add here is written out, so that all instantiations (with and without records,
+// every launch shape) round identically and a run resumed with different step blocks is
+// bitwise the same.
 __device__ __forceinline__ float3 rhs_u(float sx, float sy, float sz, float ss, float bx, float by, float bz,
                                         float al) {
-    const float cx = sy * bz - sz * by, cy = sz * bx - sx * bz, cz = sx * by - sy * bx;
-    const float sb = sx * bx + sy * by + sz * bz;
-    return make_float3(fmaf(al, fmaf(sb, sx, -ss * bx), cx), fmaf(al, fmaf(sb, sy, -ss * by), cy),
-                       fmaf(al, fmaf(sb, sz, -ss * bz), cz));
+    const float cx = fmaf(sy, bz, -(sz * by)), cy = fmaf(sz, bx, -(sx * bz)), cz = fmaf(sx, by, -(sy * bx));
+    const float sb = fmaf(sx, bx, fmaf(sy, by, sz * bz));
+    return make_float3(fmaf(al, fmaf(sb, sx, -(ss * bx)), cx), fmaf(al, fmaf(sb, sy, -(ss * by)), cy),
+                       fmaf(al, fmaf(sb, sz, -(ss * bz)), cz));
 }
 
-template <int NT, int E, int SW, int SH, int MINB, bool RECORD>
+// 1 / |v| (v = 0 is not passed)
+__device__ __forceinline__ float inv_norm(float x, float y, float z) { return rsqrtf(fmaf(x, x, fmaf(y, y, z * z))); }
+
+// Field at a staged S position: h + sum_s (J_s / mu_s) sum_{j in shell s} S_j, with P0 the
+// position in the staged plane (component planes CAPS floats apart) and m / p the own
+// column's spins of the planes below and above.  With the mask a neighbour counts only when
+// its grain code equals g (codes G0 in the same layout, gm / gp of the planes below and
+// above).
+template <bool TET, int CAPS, int SW>
+__device__ __forceinline__ float3 field_s(const FusedArgs &a, float3 h, const float *P0, float mx, float my, float mz,
+                                          float px, float py, float pz, bool mask, const uint16_t *G0, unsigned g,
+                                          unsigned gm, unsigned gp) {
+    constexpr int D0 = -SW - 1, D1 = -SW + 1, D2 = SW - 1, D3 = SW + 1;  // in-plane diagonals
+    float w[10] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+    if (mask) {
+        w[0] = G0[-1] == g;
+        w[1] = G0[1] == g;
+        w[2] = G0[-SW] == g;
+        w[3] = G0[SW] == g;
+        w[4] = gm == g;
+        w[5] = gp == g;
+        if (TET) {
+            w[6] = G0[D0] == g;
+            w[7] = G0[D1] == g;
+            w[8] = G0[D2] == g;
+            w[9] = G0[D3] == g;
+        }
+    }
+    auto comp = [&](const float *Pd, float zb, float za, float hd) {
+        if (!mask) {
+            const float nn = (Pd[-1] + Pd[1]) + (Pd[-SW] + Pd[SW]);
+            if (TET)
+                return fmaf(a.cJ[0], nn, fmaf(a.cJ[1], zb + za, fmaf(a.cJ[2], (Pd[D0] + Pd[D1]) + (Pd[D2] + Pd[D3]), hd)));
+            return fmaf(a.cJ[0], nn + (zb + za), hd);
+        }
+        const float nn = fmaf(w[0], Pd[-1], w[1] * Pd[1]) + fmaf(w[2], Pd[-SW], w[3] * Pd[SW]);
+        const float zz = fmaf(w[4], zb, w[5] * za);
+        if (TET)
+            return fmaf(a.cJ[0], nn,
+                        fmaf(a.cJ[1], zz,
+                             fmaf(a.cJ[2], fmaf(w[6], Pd[D0], w[7] * Pd[D1]) + fmaf(w[8], Pd[D2], w[9] * Pd[D3]), hd)));
+        return fmaf(a.cJ[0], nn + zz, hd);
+    };
+    return make_float3(comp(P0, mx, px, h.x), comp(P0 + CAPS, my, py, h.y), comp(P0 + 2 * CAPS, mz, pz, h.z));
+}
+
+// The same for the staged S' plane (float4 per position, .w = grain code) at Q, with the own
+// column's S' of the planes below (zm) and above (zp).
+template <bool TET, int SW>
+__device__ __forceinline__ float3 field_p(const FusedArgs &a, float3 h, const float4 *Q, const float4 &zm,
+                                          const float4 &zp, bool mask, unsigned g) {
+    if constexpr (!TET) {  // six nearest neighbours, one shell
+        const float4 l = Q[-1], r = Q[1], d = Q[-SW], u = Q[SW];
+        float w[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+        if (mask) {
+            w[0] = __float_as_uint(l.w) == g;
+            w[1] = __float_as_uint(r.w) == g;
+            w[2] = __float_as_uint(d.w) == g;
+            w[3] = __float_as_uint(u.w) == g;
+            w[4] = __float_as_uint(zm.w) == g;
+            w[5] = __float_as_uint(zp.w) == g;
+        }
+        auto comp = [&](float vl, float vr, float vd, float vu, float vm, float vp, float hd) {
+            if (!mask) return fmaf(a.cJ[0], ((vl + vr) + (vd + vu)) + (vm + vp), hd);
+            return fmaf(a.cJ[0], (fmaf(w[0], vl, w[1] * vr) + fmaf(w[2], vd, w[3] * vu)) + fmaf(w[4], vm, w[5] * vp),
+                        hd);
+        };
+        return make_float3(comp(l.x, r.x, d.x, u.x, zm.x, zp.x, h.x), comp(l.y, r.y, d.y, u.y, zm.y, zp.y, h.y),
+                           comp(l.z, r.z, d.z, u.z, zm.z, zp.z, h.z));
+    }
+    constexpr int D0 = -SW - 1, D1 = -SW + 1, D2 = SW - 1, D3 = SW + 1;
+    auto wt = [&](const float4 &v) { return mask ? (float)(__float_as_uint(v.w) == g) : 1.f; };
+    // nearest in-plane neighbours, then the planes below and above
+    float3 nn, zz;
+    {
+        const float4 l = Q[-1], r = Q[1], d = Q[-SW], u = Q[SW];
+        if (!mask) {
+            nn = make_float3((l.x + r.x) + (d.x + u.x), (l.y + r.y) + (d.y + u.y), (l.z + r.z) + (d.z + u.z));
+            zz = make_float3(zm.x + zp.x, zm.y + zp.y, zm.z + zp.z);
+        } else {
+            const float w0 = wt(l), w1 = wt(r), w2 = wt(d), w3 = wt(u), w4 = wt(zm), w5 = wt(zp);
+            nn = make_float3(fmaf(w0, l.x, w1 * r.x) + fmaf(w2, d.x, w3 * u.x), fmaf(w0, l.y, w1 * r.y) + fmaf(w2, d.y, w3 * u.y),
+                             fmaf(w0, l.z, w1 * r.z) + fmaf(w2, d.z, w3 * u.z));
+            zz = make_float3(fmaf(w4, zm.x, w5 * zp.x), fmaf(w4, zm.y, w5 * zp.y), fmaf(w4, zm.z, w5 * zp.z));
+        }
+    }
+    // in-plane diagonals (third shell)
+    const float4 q0 = Q[D0], q1 = Q[D1], q2 = Q[D2], q3 = Q[D3];
+    const float v0 = wt(q0), v1 = wt(q1), v2 = wt(q2), v3 = wt(q3);
+    const float3 dg = make_float3(fmaf(v0, q0.x, v1 * q1.x) + fmaf(v2, q2.x, v3 * q3.x),
+                                  fmaf(v0, q0.y, v1 * q1.y) + fmaf(v2, q2.y, v3 * q3.y),
+                                  fmaf(v0, q0.z, v1 * q1.z) + fmaf(v2, q2.z, v3 * q3.z));
+    return make_float3(fmaf(a.cJ[0], nn.x, fmaf(a.cJ[1], zz.x, fmaf(a.cJ[2], dg.x, h.x))),
+                       fmaf(a.cJ[0], nn.y, fmaf(a.cJ[1], zz.y, fmaf(a.cJ[2], dg.y, h.y))),
+                       fmaf(a.cJ[0], nn.z, fmaf(a.cJ[1], zz.z, fmaf(a.cJ[2], dg.z, h.z))));
+}
+
+template <bool TET, int NT, int E, int SW, int SH, int MINB, bool RECORD>
 __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     using Sh = FusedShape<NT, SW, SH>;
     constexpr int CAPS = Sh::CAPS, LPT = Sh::LPT, SLOT_F = Sh::SLOT_F;
@@ -149,7 +257,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     float *__restrict__ Sout = par ? a.Sbuf0 : a.Sbuf1;
     if (blockIdx.x == 0 && tid == 0) a.ctl->work_ctr[par ^ 1] = 0u;  // next step's counter
     const float t = (float)step * a.dt;
-    const float q = a.pref * a.dt;
+    const float q = a.pref * a.dt, qh = 0.5f * q;
     bool stop = false;  // a bounded wait ran out (decided uniformly by barrier vote)
     // The slot barriers live for the whole kernel: every thread arrives once per fill (the TMA
     // issuer with the expected byte count, per-position copies through cp.async), and each
@@ -345,32 +453,41 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                         hx[j] = fmaf(sig[j], n0, bax);
                         hy[j] = fmaf(sig[j], n1, bay);
                         hz[j] = fmaf(sig[j], n2, baz);
-                        float ex, ey, ez;
-                        if (!mask) {
-                            ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x[j] + ppx[j]);
-                            ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y[j] + ppy[j]);
-                            ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
-                                 (m1z[j] + ppz[j]);
+                        float3 B;
+                        if constexpr (TET) {
+                            B = field_s<TET, CAPS, SW>(a, make_float3(hx[j], hy[j], fmaf(a.cK, sz, hz[j])), P0, m1x[j],
+                                                       m1y[j], m1z[j], ppx[j], ppy[j], ppz[j], mask, sG + SK * CAPS + c[j],
+                                                       g0[j], gm1[j], mask ? sG[SK1 * CAPS + c[j]] : 0u);
                         } else {
-                            const uint16_t *G0 = sG + SK * CAPS + c[j];
-                            const unsigned g = g0[j];
-                            const float w0 = G0[-1] == g, w1 = G0[1] == g, w2 = G0[-SW] == g, w3 = G0[SW] == g,
-                                        w4 = gm1[j] == g, w5 = sG[SK1 * CAPS + c[j]] == g;
-                            ex = w0 * P0[-1] + w1 * P0[1] + w2 * P0[-SW] + w3 * P0[SW] + w4 * m1x[j] + w5 * ppx[j];
-                            ey = w0 * P0[CAPS - 1] + w1 * P0[CAPS + 1] + w2 * P0[CAPS - SW] + w3 * P0[CAPS + SW] +
-                                 w4 * m1y[j] + w5 * ppy[j];
-                            ez = w0 * P0[2 * CAPS - 1] + w1 * P0[2 * CAPS + 1] + w2 * P0[2 * CAPS - SW] +
-                                 w3 * P0[2 * CAPS + SW] + w4 * m1z[j] + w5 * ppz[j];
+                            float ex, ey, ez;
+                            if (!mask) {
+                                ex = ((P0[-1] + P0[1]) + (P0[-SW] + P0[SW])) + (m1x[j] + ppx[j]);
+                                ey = ((P0[CAPS - 1] + P0[CAPS + 1]) + (P0[CAPS - SW] + P0[CAPS + SW])) + (m1y[j] + ppy[j]);
+                                ez = ((P0[2 * CAPS - 1] + P0[2 * CAPS + 1]) + (P0[2 * CAPS - SW] + P0[2 * CAPS + SW])) +
+                                     (m1z[j] + ppz[j]);
+                            } else {
+                                const uint16_t *G0 = sG + SK * CAPS + c[j];
+                                const unsigned g = g0[j];
+                                const float w0 = G0[-1] == g, w1 = G0[1] == g, w2 = G0[-SW] == g, w3 = G0[SW] == g,
+                                            w4 = gm1[j] == g, w5 = sG[SK1 * CAPS + c[j]] == g;
+                                ex = fmaf(w0, P0[-1], w1 * P0[1]) + fmaf(w2, P0[-SW], w3 * P0[SW]) +
+                                     fmaf(w4, m1x[j], w5 * ppx[j]);
+                                ey = fmaf(w0, P0[CAPS - 1], w1 * P0[CAPS + 1]) + fmaf(w2, P0[CAPS - SW], w3 * P0[CAPS + SW]) +
+                                     fmaf(w4, m1y[j], w5 * ppy[j]);
+                                ez = fmaf(w0, P0[2 * CAPS - 1], w1 * P0[2 * CAPS + 1]) +
+                                     fmaf(w2, P0[2 * CAPS - SW], w3 * P0[2 * CAPS + SW]) + fmaf(w4, m1z[j], w5 * ppz[j]);
+                            }
+                            B = make_float3(fmaf(a.cJ[0], ex, hx[j]), fmaf(a.cJ[0], ey, hy[j]),
+                                            fmaf(a.cJ[0], ez, fmaf(a.cK, sz, hz[j])));
                         }
-                        const float ss = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
-                        const float3 u = rhs_u(sx, sy, sz, ss, fmaf(a.cJ, ex, hx[j]), fmaf(a.cJ, ey, hy[j]),
-                                               fmaf(a.cJ, ez, fmaf(a.cK, sz, hz[j])), a.alpha);
-                        const float fx = q * u.x, fy = q * u.y, fz = q * u.z;
-                        anx[j] = fmaf(0.5f, fx, sx);
-                        any[j] = fmaf(0.5f, fy, sy);
-                        anz[j] = fmaf(0.5f, fz, sz);
-                        const float npx = sx + fx, npy = sy + fy, npz = sz + fz;
-                        const float inv = rsqrtf(npx * npx + npy * npy + npz * npz);
+                        const float ss = fmaf(sx, sx, fmaf(sy, sy, sz * sz));  // |S|^2
+                        const float3 u = rhs_u(sx, sy, sz, ss, B.x, B.y, B.z, a.alpha);
+                        // S + dt f / 2 (the corrector's base) and S + dt f, dt f = q u
+                        anx[j] = fmaf(qh, u.x, sx);
+                        any[j] = fmaf(qh, u.y, sy);
+                        anz[j] = fmaf(qh, u.z, sz);
+                        const float npx = fmaf(q, u.x, sx), npy = fmaf(q, u.y, sy), npz = fmaf(q, u.z, sz);
+                        const float inv = inv_norm(npx, npy, npz);
                         sp[j] = make_float4(npx * inv, npy * inv, npz * inv, __uint_as_float(g0[j]));
                     }
                     sP[SK * CAPS + c[j]] = sp[j];
@@ -386,28 +503,34 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                     const float4 *Q = sP + SKM1 * CAPS + c[j];
                     const float4 v = Q[0];
                     if (!nonzero3(v.x, v.y, v.z)) continue;
-                    const float4 l = Q[-1], r = Q[1], d = Q[-SW], u4 = Q[SW];
-                    const float4 zm = sP[SKM2 * CAPS + c[j]], zp = sp[j];
-                    float ex, ey, ez;
-                    if (!mask) {
-                        ex = ((l.x + r.x) + (d.x + u4.x)) + (zm.x + zp.x);
-                        ey = ((l.y + r.y) + (d.y + u4.y)) + (zm.y + zp.y);
-                        ez = ((l.z + r.z) + (d.z + u4.z)) + (zm.z + zp.z);
-                    } else {
-                        const unsigned g = __float_as_uint(v.w);
-                        const float w0 = __float_as_uint(l.w) == g, w1 = __float_as_uint(r.w) == g,
-                                    w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u4.w) == g,
-                                    w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(zp.w) == g;
-                        ex = w0 * l.x + w1 * r.x + w2 * d.x + w3 * u4.x + w4 * zm.x + w5 * zp.x;
-                        ey = w0 * l.y + w1 * r.y + w2 * d.y + w3 * u4.y + w4 * zm.y + w5 * zp.y;
-                        ez = w0 * l.z + w1 * r.z + w2 * d.z + w3 * u4.z + w4 * zm.z + w5 * zp.z;
-                    }
                     // S' is a unit vector: S'.S' = 1 in the damping term
-                    const float3 u = rhs_u(v.x, v.y, v.z, 1.f, fmaf(a.cJ, ex, hmx[j]), fmaf(a.cJ, ey, hmy[j]),
-                                           fmaf(a.cJ, ez, fmaf(a.cK, v.z, hmz[j])), a.alpha);
-                    const float qh = 0.5f * q;
+                    float3 B;
+                    if constexpr (TET) {
+                        B = field_p<TET, SW>(a, make_float3(hmx[j], hmy[j], fmaf(a.cK, v.z, hmz[j])), Q,
+                                             sP[SKM2 * CAPS + c[j]], sp[j], mask, __float_as_uint(v.w));
+                    } else {
+                        const float4 l = Q[-1], r = Q[1], d = Q[-SW], u4 = Q[SW];
+                        const float4 zm = sP[SKM2 * CAPS + c[j]], zp = sp[j];
+                        float ex, ey, ez;
+                        if (!mask) {
+                            ex = ((l.x + r.x) + (d.x + u4.x)) + (zm.x + zp.x);
+                            ey = ((l.y + r.y) + (d.y + u4.y)) + (zm.y + zp.y);
+                            ez = ((l.z + r.z) + (d.z + u4.z)) + (zm.z + zp.z);
+                        } else {
+                            const unsigned g = __float_as_uint(v.w);
+                            const float w0 = __float_as_uint(l.w) == g, w1 = __float_as_uint(r.w) == g,
+                                        w2 = __float_as_uint(d.w) == g, w3 = __float_as_uint(u4.w) == g,
+                                        w4 = __float_as_uint(zm.w) == g, w5 = __float_as_uint(zp.w) == g;
+                            ex = fmaf(w0, l.x, w1 * r.x) + fmaf(w2, d.x, w3 * u4.x) + fmaf(w4, zm.x, w5 * zp.x);
+                            ey = fmaf(w0, l.y, w1 * r.y) + fmaf(w2, d.y, w3 * u4.y) + fmaf(w4, zm.y, w5 * zp.y);
+                            ez = fmaf(w0, l.z, w1 * r.z) + fmaf(w2, d.z, w3 * u4.z) + fmaf(w4, zm.z, w5 * zp.z);
+                        }
+                        B = make_float3(fmaf(a.cJ[0], ex, hmx[j]), fmaf(a.cJ[0], ey, hmy[j]),
+                                        fmaf(a.cJ[0], ez, fmaf(a.cK, v.z, hmz[j])));
+                    }
+                    const float3 u = rhs_u(v.x, v.y, v.z, 1.f, B.x, B.y, B.z, a.alpha);
                     float ox = fmaf(qh, u.x, amx[j]), oy = fmaf(qh, u.y, amy[j]), oz = fmaf(qh, u.z, amz[j]);
-                    const float inv = rsqrtf(ox * ox + oy * oy + oz * oz);
+                    const float inv = inv_norm(ox, oy, oz);
                     ox *= inv;
                     oy *= inv;
                     oz *= inv;
@@ -482,15 +605,15 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
 
 // Opt in to the variant's dynamic shared memory (done before any stream capture, when the
 // work list is built).
-template <int NT, int E, int SW, int SH, int MINB>
+template <bool TET, int NT, int E, int SW, int SH, int MINB>
 static cudaError_t ensure_attrs() {
     using Sh = FusedShape<NT, SW, SH>;
     static bool init = false;
     if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<NT, E, SW, SH, MINB, false>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused<NT, E, SW, SH, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Sh::smem);
         if (e != cudaSuccess) return e;
         init = true;
@@ -498,24 +621,24 @@ static cudaError_t ensure_attrs() {
     return cudaSuccess;
 }
 
-template <int NT, int E, int SW, int SH, int MINB>
+template <bool TET, int NT, int E, int SW, int SH, int MINB>
 static cudaError_t launch_variant(const FusedArgs &a, int grid, bool record, cudaStream_t st) {
     using Sh = FusedShape<NT, SW, SH>;
-    cudaError_t e = ensure_attrs<NT, E, SW, SH, MINB>();
+    cudaError_t e = ensure_attrs<TET, NT, E, SW, SH, MINB>();
     if (e != cudaSuccess) return e;
     if (record)
-        k_fused<NT, E, SW, SH, MINB, true><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<TET, NT, E, SW, SH, MINB, true><<<grid, NT, Sh::smem, st>>>(a);
     else
-        k_fused<NT, E, SW, SH, MINB, false><<<grid, NT, Sh::smem, st>>>(a);
+        k_fused<TET, NT, E, SW, SH, MINB, false><<<grid, NT, Sh::smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NT, int E, int SW, int SH, int MINB>
+template <bool TET, int NT, int E, int SW, int SH, int MINB>
 static int blocks_per_sm() {
     using Sh = FusedShape<NT, SW, SH>;
     int n = 0;
-    if (ensure_attrs<NT, E, SW, SH, MINB>() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<NT, E, SW, SH, MINB, false>, NT, Sh::smem) !=
+    if (ensure_attrs<TET, NT, E, SW, SH, MINB>() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<TET, NT, E, SW, SH, MINB, false>, NT, Sh::smem) !=
         cudaSuccess)
         return 0;
     return n;
@@ -529,32 +652,19 @@ static int blocks_per_sm() {
 #define HAMR_FUSED_VARIANTS(X) \
     X(0, 512, 1, 36, 24, 2) X(1, 1024, 1, 68, 24, 1) X(2, 256, 1, 36, 14, 3) X(3, 256, 2, 36, 24, 2)
 
-cudaError_t launch_fused_step(int v, const FusedArgs &a, int grid, bool record, cudaStream_t st) {
+template <bool TET>
+cudaError_t launch_fused_lattice(int v, const FusedArgs &a, int grid, bool record, cudaStream_t st) {
 #define X(I, NT, E, SW, SH, MINB) \
-    if (v == I) return launch_variant<NT, E, SW, SH, MINB>(a, grid, record, st);
+    if (v == I) return launch_variant<TET, NT, E, SW, SH, MINB>(a, grid, record, st);
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-bool fused_variant(int v, FusedVariant &out) {
+template <bool TET>
+int fused_blocks_lattice(int v) {
 #define X(I, NT, E, SW, SH, MINB) \
-    if (v == I) {                 \
-        out.threads = NT;         \
-        out.columns = NT * E;     \
-        out.pitch = SW;           \
-        out.rows = SH;            \
-        out.staged = SW * SH;     \
-        return true;              \
-    }
-    HAMR_FUSED_VARIANTS(X)
-#undef X
-    return false;
-}
-
-int fused_max_blocks_per_sm(int v) {
-#define X(I, NT, E, SW, SH, MINB) \
-    if (v == I) return blocks_per_sm<NT, E, SW, SH, MINB>();
+    if (v == I) return blocks_per_sm<TET, NT, E, SW, SH, MINB>();
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return 0;

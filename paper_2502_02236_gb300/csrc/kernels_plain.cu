@@ -10,8 +10,8 @@
 // adds the new spin to its grain's FP64 sum.
 //
 // This is the plain path: FP64 for every precision-FP64 handle, and FP32 for handles that
-// use a neighbour list (L1_0, or SC with an explicit list).  Neighbours come from the
-// implicit 6-site stencil (bonds only between equal grain codes) or from the packed list.
+// use a neighbour list.  Neighbours come from the lattice's implicit stencil (bonds only
+// between equal grain codes) or from the packed list.
 #include "device_common.cuh"
 
 namespace hamr {
@@ -108,20 +108,22 @@ __device__ __forceinline__ void exchange(const PlainArgs<Real> &a, const Replica
             ez += cj * V[2 * NS + j];
         }
     } else {
-        const Real cj = (Real)a.ph.cJ[0];
-        const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        // the lattice's implicit stencil: SC, 6 nearest neighbours in one shell; L1_0 Fe
+        // sublattice, 4 in-plane nearest (shell 0), 2 out of plane (shell 1) and 4 in-plane
+        // diagonals (shell 2)
+        const bool tet = a.ph.lattice == HAMR_LATTICE_L10;
+        const int d[10][4] = {{-1, 0, 0, 0}, {1, 0, 0, 0},  {0, -1, 0, 0},  {0, 1, 0, 0},  {0, 0, -1, 1},
+                              {0, 0, 1, 1},  {-1, -1, 0, 2}, {1, -1, 0, 2}, {-1, 1, 0, 2}, {1, 1, 0, 2}};
+        const int nb = tet ? 10 : 6;
+        for (int k = 0; k < nb; ++k) {
             const long long j = stencil_slot(R, a.ph.per, q, d[k][0], d[k][1], d[k][2]);
             if (j >= 0 && a.gcode[j] == g) {
-                ex += V[j];
-                ey += V[NS + j];
-                ez += V[2 * NS + j];
+                const Real cj = (Real)a.ph.cJ[tet ? d[k][3] : 0];
+                ex += cj * V[j];
+                ey += cj * V[NS + j];
+                ez += cj * V[2 * NS + j];
             }
         }
-        ex *= cj;
-        ey *= cj;
-        ez *= cj;
     }
 }
 

@@ -153,7 +153,8 @@ def workload(name, **over):
                +/-0.8 T trapezoidal field with 20 nm bits, 1e5 steps of 0.1 fs, FP32;
     l10_window L1_0 Fe sublattice of the fct cell a = 0.385 nm, c = 0.371 nm over a
                60x100x10 nm window (220x367x27 sites), J1 = 6.7e-21 J, J2 = J1/2, J3 = J1/10,
-               ku = 2.6e-22 J, 7 nm grains, laser and field as sc_track, FP32;
+               ku = 2.6e-22 J, 7 nm grains, laser and field as sc_track, FP32, on the
+               implicit three-shell stencil (neighbours="csr" gives the list path);
     ensemble256 256 independent SC grain arrays, sides 32..96, 8..32 layers, uniform T in
                500..900 K, 0.8 T along -z, 8 nm grains, FP32, 1e5 steps.
     """
@@ -180,7 +181,7 @@ def workload(name, **over):
         ap = la / math.sqrt(2.0)
         nx, ny, nz = int(60e-9 / ap), int(100e-9 / ap), int(round(10e-9 / lc))
         g2 = voronoi_grains(nx, ny, ap, ap, 7e-9, 1e-9, 12)
-        w = dict(base, lattice="l10", neighbours="csr", a=la, c=lc, ku=KU_L10,
+        w = dict(base, lattice="l10", neighbours="stencil", a=la, c=lc, ku=KU_L10,
                  J=[J_SC, 0.5 * J_SC, 0.1 * J_SC], steps=100000, replicas=[dict(
                      dims=(nx, ny, nz), seed=12, grain=columnar(g2, nz), n_grains=int(g2.max()) + 1,
                      T=dict(T_amb=300.0, T_peak=800.0, fwhm=50e-9, x0=nx * ap / 2, y0=ny * ap / 2, vx=20.0),

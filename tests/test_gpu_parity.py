@@ -239,6 +239,41 @@ def test_l10_three_shells(prec, tol):
     assert max_abs(Mg, Mo) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_l10_stencil_three_shells(prec, tol):
+    """The implicit L1_0 stencil (the fused kernel in FP32, the two-pass path in FP64)
+    against the oracle's geometric shells: granular, laser, field, periodic in y."""
+    w = l10_piece(30, 26, 7, seed=5)
+    (g, o, Mg, Mo), = run_both(w, 300, precision=prec, neighbours="stencil", record_every=50)
+    assert max_abs(g, o) < tol
+    assert max_abs(Mg, Mo) < tol
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_l10_stencil_every_tile_touching_grains(tile):
+    """The fused L1_0 kernel in every compiled shape, open and fully periodic lattices, with
+    grains that touch (no boundary layer, so the exchange mask decides every bond)."""
+    for periodic in ((False, False, False), (True, True, True)):
+        la, lc = 0.385e-9, 0.371e-9
+        ap = la / np.sqrt(2)
+        g2 = I.voronoi_grains(40, 34, ap, ap, 2.5e-9, 0.0, 8)
+        rep = dict(dims=(40, 34, 5), seed=77, grain=I.columnar(g2, 5), n_grains=int(g2.max()) + 1, init="random",
+                   T=dict(T_amb=500.0), field=dict(B0=0.5, direction=(0.3, 0, -1)))
+        w = dict(lattice="l10", precision="fp32", neighbours="stencil", a=la, c=lc, periodic=periodic,
+                 mu_s=I.MU_S, ku=I.KU_L10, alpha=0.1, dt=1e-16, J=[I.J_SC, 0.5 * I.J_SC, 0.1 * I.J_SC],
+                 replicas=[rep])
+        (g, o, _, _), = run_both(w, 60, tile=tile)
+        assert max_abs(g, o) < TOL32, (tile, periodic)
+
+
+def test_l10_list_matches_stencil():
+    w = l10_piece(22, 18, 5, seed=6)
+    (gs, o, _, _), = run_both(w, 100, neighbours="stencil")
+    (gc, _, _, _), = run_both(w, 100, neighbours="csr")
+    assert max_abs(gs, gc) < 1e-12
+    assert max_abs(gc, o) < TOL64
+
+
 def test_sc_list_matches_stencil():
     w = workload_of([tiny_track(31, 22, 7, seed=9)], precision="fp64", periodic=(True, False, True))
     (gs, o, _, _), = run_both(w, 100)
