@@ -271,6 +271,22 @@ def cpu_baseline(w, seconds):
     return n * steps / el, reps, n, steps, el
 
 
+def cpu_baseline_one_core(workload, seconds):
+    """The same oracle timing on one host core (OpenMP limited to one thread in a child
+    process); None if the child fails."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; from paper_2502_02236_gb300 import inputs as I; "
+            "v, reps, n, steps, el = bench.cpu_baseline(I.workload(%r), %r); "
+            "print(json.dumps({'value': v, 'unit': 'spin-steps/s', 'cores': 1, "
+            "'sample': 'replicas 0..%%d (%%d sites), %%d steps in %%.1f s' %% (reps[-1], n, steps, el)}))"
+            % (ROOT, workload, float(seconds)))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -315,6 +331,7 @@ def main():
     t_launch = ms_k / K / 1e3
     achieved = BYTES_PER_SITE_FP32 * n_sites / t_launch / 1e9
     peak, peak_kind = peaks()
+    traffic = kernel_traffic() if args.workload == "ensemble256" else None
     assert lat.check_finite()
     launches = K + K // rec
 
@@ -328,7 +345,8 @@ def main():
            "magnetic_spin_steps_per_s": n_mag * K * dist.world / (ms / 1e3),
            "gpu_launches": launches,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": kernel_traffic(),
+                        "frac": achieved / peak, "traffic": traffic,
+                        "traffic_gbs": traffic / t_launch / 1e9 if traffic else None,
                         "peak_source": peak_kind, "kernel": "k_fused", "avg_launch_ms": t_launch * 1e3,
                         "bytes_per_site": BYTES_PER_SITE_FP32},
            "clocks": clk}
@@ -376,6 +394,9 @@ def main():
         out["cpu_baseline"] = {"value": v, "unit": "spin-steps/s", "cores": os.cpu_count(), "kind": "oracle",
                                "sample": "FP64 oracle, replicas 0..%d of the workload (%d sites), %d steps in %.1f s"
                                          % (reps[-1], n, steps, el)}
+        one = cpu_baseline_one_core(args.workload, max(3.0, args.cpu_seconds / 3))
+        if one:
+            out["cpu_baseline"]["one_core"] = one
     lat.close()
     if dist.rank == 0:
         print(json.dumps(out), flush=True)

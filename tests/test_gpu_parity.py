@@ -249,21 +249,23 @@ def test_l10_stencil_three_shells(prec, tol):
     assert max_abs(Mg, Mo) < tol
 
 
-@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("tile", TILES + ["fp64"])
 def test_l10_stencil_every_tile_touching_grains(tile):
-    """The fused L1_0 kernel in every compiled shape, open and fully periodic lattices, with
-    grains that touch (no boundary layer, so the exchange mask decides every bond)."""
+    """The fused L1_0 kernel in every compiled shape (and the FP64 two-pass stencil), open and
+    fully periodic lattices, with grains that touch (no boundary layer, so the exchange mask
+    decides every bond)."""
+    prec, tol = ("fp64", TOL64) if tile == "fp64" else ("fp32", TOL32)
     for periodic in ((False, False, False), (True, True, True)):
         la, lc = 0.385e-9, 0.371e-9
         ap = la / np.sqrt(2)
         g2 = I.voronoi_grains(40, 34, ap, ap, 2.5e-9, 0.0, 8)
         rep = dict(dims=(40, 34, 5), seed=77, grain=I.columnar(g2, 5), n_grains=int(g2.max()) + 1, init="random",
                    T=dict(T_amb=500.0), field=dict(B0=0.5, direction=(0.3, 0, -1)))
-        w = dict(lattice="l10", precision="fp32", neighbours="stencil", a=la, c=lc, periodic=periodic,
+        w = dict(lattice="l10", precision=prec, neighbours="stencil", a=la, c=lc, periodic=periodic,
                  mu_s=I.MU_S, ku=I.KU_L10, alpha=0.1, dt=1e-16, J=[I.J_SC, 0.5 * I.J_SC, 0.1 * I.J_SC],
                  replicas=[rep])
-        (g, o, _, _), = run_both(w, 60, tile=tile)
-        assert max_abs(g, o) < TOL32, (tile, periodic)
+        (g, o, _, _), = run_both(w, 60, tile=None if tile == "fp64" else tile)
+        assert max_abs(g, o) < tol, (tile, periodic)
 
 
 def test_l10_list_matches_stencil():
