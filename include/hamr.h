@@ -110,9 +110,9 @@ int hamr_set_neighbour_shells(hamr_t h, int32_t n_shells, const double *J);
 
 /* Replace the neighbour list of one replica (HAMR_NBR_CSR only): row_ptr[n+1], col[nnz]
  * site indices of that replica (x fastest), shell[nnz] in [0, n_shells).  At most 32
- * neighbours per site.  Bonds touching a non-magnetic site are ignored.  Bonds must be
- * symmetric for energy conservation but this is not checked.  Errors: ARG, STATE
- * (stencil handle), OOM. */
+ * neighbours per site.  Bonds touching a non-magnetic site are ignored.  Every bond i -> j
+ * of shell s must have its partner j -> i of the same shell (J_ij = J_ji); a list without
+ * is rejected.  Errors: ARG, STATE (stencil handle), OOM. */
 int hamr_set_csr(hamr_t h, int32_t replica, const int32_t *row_ptr, const int32_t *col,
                  const uint8_t *shell);
 

@@ -11,11 +11,20 @@
 #include <memory>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hamr_internal.h"
 
 using namespace hamr;
 
 namespace {
+
+// NVTX range over a host call (setup, step blocks, record collection), visible in a timeline
+// profiler; free when no profiler is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 thread_local std::string g_create_err = "no error";
 
@@ -381,6 +390,7 @@ int build_maps(hamr_t h, int r, const FusedVariant &v, CUtensorMap out[2]) {
 // lies inside the lattice (or wraps on a periodic axis) and holds a magnetic site on some
 // plane; interior columns come first.
 int build_items(hamr_t h) {
+    Range nv("hamr build_items");
     FusedVariant v;
     if (!fused_variant(h->variant, v)) return fail(h, HAMR_ERR_ARG, "unknown kernel variant %d", h->variant);
     std::vector<WorkItem> items;
@@ -600,6 +610,7 @@ int run_block(hamr_t h, int G, bool record) {
 }
 
 int collect_records(hamr_t h) {
+    Range nv("hamr collect_records");
     CK(h, cudaStreamSynchronize(h->stream));
     Ctl c;
     CK(h, cudaMemcpy(&c, h->ctl_d, sizeof(Ctl), cudaMemcpyDeviceToHost));
@@ -629,6 +640,7 @@ int collect_records(hamr_t h) {
 
 int steps_impl(hamr_t h, int64_t n_steps, int32_t record_every, bool sync) {
     if (!h) return HAMR_ERR_ARG;
+    Range nv("hamr sllg_heun_steps");
     if (n_steps < 0 || record_every < 0) return fail(h, HAMR_ERR_ARG, "n_steps and record_every must be >= 0");
     if (!h->shells_set) return fail(h, HAMR_ERR_STATE, "exchange shells not set (hamr_set_neighbour_shells)");
     if (h->max_user_shell >= h->ph.n_shells)
@@ -914,6 +926,17 @@ int hamr_set_csr(hamr_t h, int32_t replica, const int32_t *row_ptr, const int32_
         if (col[e] < 0 || col[e] >= n) return fail(h, HAMR_ERR_ARG, "col[%d] = %d out of range", e, col[e]);
         if (shell[e] >= MAX_SHELLS) return fail(h, HAMR_ERR_ARG, "shell[%d] = %d out of range", e, shell[e]);
     }
+    // every bond i -> j of shell s needs its partner j -> i of the same shell (J_ij = J_ji,
+    // which the energy and its conservation rely on)
+    for (long long i = 0; i < n; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col[e];
+            bool found = false;
+            for (int f = row_ptr[j]; f < row_ptr[j + 1] && !found; ++f) found = col[f] == i && shell[f] == shell[e];
+            if (!found)
+                return fail(h, HAMR_ERR_ARG, "bond %lld -> %d (shell %d) has no partner %d -> %lld", i, j, shell[e], j,
+                            i);
+        }
     DeviceGuard dg(h->device);
     if ((int)h->ucsr_rp.size() < h->R) {
         h->ucsr_rp.resize(h->R);
@@ -946,6 +969,7 @@ int hamr_set_csr(hamr_t h, int32_t replica, const int32_t *row_ptr, const int32_
 }
 
 int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t n_grains) {
+    Range nv("hamr set_grain_map");
     if (bad_replica(h, replica)) return h ? fail(h, HAMR_ERR_ARG, "bad replica %d", replica) : HAMR_ERR_ARG;
     if (!grain || n_grains < 0 || n_grains > 65534) return fail(h, HAMR_ERR_ARG, "bad grain map or n_grains");
     ReplicaDev &R = h->reps_h[replica];
@@ -1282,6 +1306,7 @@ int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged) {
 
 int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     if (!h) return HAMR_ERR_ARG;
+    Range nv("hamr autotune");
     if (steps_per_trial < 1) return fail(h, HAMR_ERR_ARG, "steps_per_trial must be >= 1");
     if (!fused_mode(h)) return HAMR_OK;  // the two-pass path has a single launch shape
     if (!h->shells_set) return fail(h, HAMR_ERR_STATE, "exchange shells not set");

@@ -418,3 +418,55 @@ def test_full_size_ensemble_sampled():
         want = orc.step_sites(oracle_params(w, r), w["replicas"][r]["grain"], S0[r], 0, sites)
         worst = max(worst, max_abs(lat.read_moments(r)[sites], want))
     assert worst < TOL32
+
+
+# --------------------------------------------------------------------------- degenerate inputs
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_all_void_replica_zero_steps_and_ragged_batch(prec, tol):
+    """A batch holding a replica with no magnetic site at all and a 1-site-thick one: zero
+    steps change nothing; after steps the void replica stays zero with M = 0, and the others
+    match the oracle."""
+    reps = uneven_replicas()[:3]
+    void = dict(dims=(9, 7, 3), seed=5, grain=np.full(9 * 7 * 3, -1, dtype=np.int32), n_grains=1, init="random",
+                T=dict(T_amb=300.0))
+    thin = dict(dims=(13, 1, 1), seed=6, init="random", T=dict(T_amb=300.0), field=dict(B0=1.0, direction=(0, 0, 1)))
+    reps = [void] + reps + [thin]
+    w = workload_of(reps, precision=prec)
+    S0 = [initial(rep) for rep in reps]
+    lat = gpu_lattice(w, S0=S0)
+    lat.sllg_heun_steps(0, 5)
+    for r in range(len(reps)):
+        assert np.array_equal(lat.read_moments(r), S0[r].astype(np.float32).astype(np.float64)
+                              if prec == "fp32" else S0[r])
+    lat.close()
+    outs = run_both(w, 40, S0=S0, record_every=20)
+    g, o, Mg, Mo = outs[0]
+    assert not np.any(g) and not np.any(o)           # void: nothing to move
+    assert np.array_equal(Mg, np.zeros((2, 3)))      # M of a replica without magnetic sites
+    for r, (g, o, Mg, Mo) in enumerate(outs[1:], 1):
+        assert max_abs(g, o) < tol, r
+        assert max_abs(Mg, Mo) < tol, r
+
+
+def test_call_order_and_list_checks():
+    """Stepping before the exchange shells are set is a STATE error; a neighbour list whose
+    bonds have no partner is rejected with ARG and leaves the handle usable."""
+    from paper_2502_02236_gb300 import hamr
+    rep = tiny_track(12, 10, 4, seed=3)
+    w = workload_of([rep], precision="fp64", neighbours="csr")
+    lat = gpu_lattice(w)
+    o = oracle_for(w, 0)
+    rp, col, sh = o.neighbours()
+    bad = sh.astype(np.uint8).copy()
+    bad[0] = (bad[0] + 1) % 2                       # one bond in another shell than its partner
+    with pytest.raises(hamr.HamrError) as e:
+        lat.set_csr(0, rp.astype(np.int32), col.astype(np.int32), bad)
+    assert e.value.code == hamr.ERR_ARG
+    lat.set_csr(0, rp.astype(np.int32), col.astype(np.int32), sh.astype(np.uint8))
+    lat.sllg_heun_steps(5)
+    lat.close()
+    from paper_2502_02236_gb300.hamr import Lattice
+    with Lattice([(8, 8, 2)], [1], precision="fp32", a=0.25e-9, mu_s=I.MU_S, ku=I.KU_SC, alpha=0.1, dt=1e-16) as fresh:
+        with pytest.raises(hamr.HamrError) as e:
+            fresh.sllg_heun_steps(1)
+        assert e.value.code == hamr.ERR_STATE
