@@ -8,16 +8,20 @@
 // Work item = a block of bx x by columns of one replica spanning all nz planes.  The CTA
 // stages, plane by plane, the spins of the block plus a two-column halo in shared memory and
 // marches up the planes.  Staging runs three planes ahead of the march through a four-slot
-// ring with one mbarrier per slot: one thread issues a TMA tile copy of the three spin
-// components (zero-filled beyond open edges); replicas whose blocks wrap around a periodic
-// edge, or whose grains touch, are staged instead by per-position cp.async copies that arrive
-// on the same mbarriers.  At march step k the CTA
-//   1. starts staging plane k+3 into the slot that plane k-1 has left;
-//   2. waits for plane k+1;
-//   3. predicts S' on plane k for every listed column: the block's interior and its
+// ring with one mbarrier per slot: one thread (the waiter) issues a TMA tile copy of the
+// three spin components (zero-filled beyond open edges), arriving once for the whole CTA;
+// replicas whose blocks wrap around a periodic edge, or whose grains touch, are staged instead
+// by per-position cp.async copies of every thread that arrive on the same mbarriers.  Only the
+// warps that hold list entries march (all of them for per-position copies); the waiter is lane
+// 0 of the last of them, whose columns are mostly halo columns with no corrector work.  At
+// march step k the marching warps
+//   1. start staging plane k+3 into the slot that plane k-1 has left;
+//   2. predict S' on plane k for every listed column: the block's interior and its
 //      one-column halo (corners included), so the corrector never needs another CTA's S';
-//   4. synchronises once;
-//   5. corrects plane k-1 on the interior columns from the S' planes k-2, k-1 (shared
+//   3. let the waiter wait until plane k+2 has landed (the barrier that follows makes it
+//      visible to every thread for the next step);
+//   4. synchronise once (a named barrier over the marching warps);
+//   5. correct plane k-1 on the interior columns from the S' planes k-2, k-1 (shared
 //      memory) and k (the thread's own, in registers).
 // With four S and four S' slots no other barrier is needed: the next step's writes go to
 // slots that no thread can still be reading.  The four slot mbarriers are initialised once
@@ -53,7 +57,7 @@ struct FusedShape {
     // one S slot: the TMA box [3 components][SH rows][SW columns], rounded to 128 B
     static constexpr int SLOT_F = ((3 * CAPS * 4 + 127) / 128) * 128 / 4;
     static constexpr size_t smem = 128 + sizeof(float) * NSLOT * SLOT_F + sizeof(float4) * NSLOT * CAPS +
-                                   sizeof(uint16_t) * NSLOT * CAPS;
+                                   sizeof(uint16_t) * NSLOT * CAPS + sizeof(int) * CAPS;
 };
 
 template <int V>
@@ -91,8 +95,25 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned b
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+// one arrival that stands for `count` threads, with the byte count the TMA copy will deliver
+__device__ __forceinline__ void mbar_expect_tx_n(unsigned long long *b, unsigned bytes, unsigned count) {
+    asm volatile(
+        "mbarrier.expect_tx.shared::cta.b64 [%0], %1;\n"
+        "mbarrier.arrive.shared::cta.b64 _, [%0], %2;\n" ::"r"(smem_u32(b)),
+        "r"(bytes), "r"(count)
+        : "memory");
+}
+
+// barrier `id` over the first `nthr` threads of the CTA (a multiple of 32); true on every
+// participant when any of them passed v = true
+__device__ __forceinline__ bool bar_or(int id, int nthr, bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(id), "r"(nthr)
+        : "memory");
+    return r != 0;
 }
 
 // this thread's earlier cp.async copies arrive on b once they have landed
@@ -245,10 +266,16 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     float *sS = reinterpret_cast<float *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);  // [4][SLOT_F]
     float4 *sP = reinterpret_cast<float4 *>(sS + NSLOT * SLOT_F);                          // [4][CAPS]
     uint16_t *sG = reinterpret_cast<uint16_t *>(sP + NSLOT * CAPS);                        // [4][CAPS]
+    int *sL = reinterpret_cast<int *>(sG + NSLOT * CAPS);  // [CAPS] per-position copy offsets
     __shared__ int s_item;
     __shared__ uint4 s_rk[5];  // Philox round keys of the current replica
     __shared__ __align__(8) unsigned long long s_bar[NSLOT];
-
+    // staging state that only thread 0 uses (kept out of every thread's registers): the tensor
+    // map and origin of the current item's TMA box, the phase parity of the next phase of each
+    // slot barrier, and the highest plane staged and the highest awaited
+    __shared__ const CUtensorMap *s_map;
+    __shared__ int s_xs, s_ys, s_ph, s_hi_issued, s_hi_waited;
+    __shared__ float4 s_ba;  // applied field B_app(t) of the current item
     const int tid = threadIdx.x;
     const long long NS = a.NS;
     const long long step = a.ctl->step + a.step_off;
@@ -259,10 +286,11 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     const float t = (float)step * a.dt;
     const float q = a.pref * a.dt, qh = 0.5f * q;
     bool stop = false;  // a bounded wait ran out (decided uniformly by barrier vote)
-    // The slot barriers live for the whole kernel: every thread arrives once per fill (the TMA
-    // issuer with the expected byte count, per-position copies through cp.async), and each
-    // thread tracks the parity of the next phase of every slot in ph.
-    unsigned ph = 0;
+    // The slot barriers live for the whole kernel and expect NT arrivals per fill: the TMA
+    // issuer arrives once for all NT threads with the expected byte count, per-position copies
+    // arrive through cp.async from every thread.  The parity of the next phase of every slot
+    // is kept in s_ph (only the waiter of an item reads or changes it).
+    if (tid == 0) s_ph = 0;
     if (tid < NSLOT) mbar_init(&s_bar[tid], (unsigned)NT);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 
@@ -281,13 +309,34 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         const bool mask = R.cross_grain != 0;
         const bool tma = (W.stage & 1) != 0;
         const int xs = W.x0 - 2 - (W.stage >> 8), ys = W.y0 - 2;  // staged-region origin
-        const CUtensorMap *map = a.maps + 2 * W.r + par;
+        if (tid == 0) {
+            s_map = a.maps + 2 * W.r + par;
+            s_xs = xs;
+            s_ys = ys;
+            s_hi_issued = s_hi_waited = -3;
+            const float bapp = R.fB0 * field_polarity_f(R, a.bits, t);
+            s_ba = make_float4(bapp * R.fdir[0], bapp * R.fdir[1], bapp * R.fdir[2], 0.f);
+        }
         if (tid < 5) {
             const unsigned k0 = R.key0 + 2u * tid * 0x9E3779B9u, k1 = R.key1 + 2u * tid * 0xBB67AE85u;
             s_rk[tid] = make_uint4(k0, k1, k0 + 0x9E3779B9u, k1 + 0xBB67AE85u);
         }
         // S' (and its grain code) of unlisted positions must read as 0 for the whole item
         for (int i = tid; i < NSLOT * CAPS; i += NT) sP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // per-position copies: each position's column offset within a plane (-1: zero-filled,
+        // -2: outside the block's staged region)
+        if (!tma)
+            for (int idx = tid; idx < CAPS; idx += NT) {
+                const int sx = idx % SW, sy = idx / SW;
+                int lofs = -2;
+                if (sx < bx + 4 && sy < by + 4) {
+                    bool in = true;
+                    const int cx = wrap_coord(xs + sx, nx, a.per[0], in);
+                    const int cy = wrap_coord(ys + sy, ny, a.per[1], in);
+                    lofs = in ? cx + px * cy : -1;
+                }
+                sL[idx] = lofs;
+            }
         __syncthreads();
 
         // this thread's list entries tid, tid + NT, ... (site and storage indices fit in 32
@@ -318,21 +367,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                 ocol[j] = off + wx + px * wy;
             }
         }
-        // per-position copies (fallback): column offsets within a plane (-1: zero-filled,
-        // -2: outside the block's staged region)
-        int lofs[LPT];
-#pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-            const int idx = tid + l * NT;
-            const int sx = idx % SW, sy = idx / SW;
-            lofs[l] = -2;
-            if (!tma && idx < CAPS && sx < bx + 4 && sy < by + 4) {
-                bool ok = true;
-                const int cx = wrap_coord(xs + sx, nx, a.per[0], ok);
-                const int cy = wrap_coord(ys + sy, ny, a.per[1], ok);
-                lofs[l] = ok ? cx + px * cy : -1;
-            }
-        }
+        // Only the warps that hold list entries march; the others wait at the end of the item.
+        // Per-position copies need every thread, so those items march with the whole CTA.  Lane
+        // 0 of the last marching warp, whose columns are mostly halo columns without a corrector
+        // stage, issues the TMA fills and waits for them (the waiter).
+        const int nmarch = tma ? min(NT, (n_act + 31) & ~31) : NT;
+        const int waiter = nmarch - 32;
         // stage plane p into ring slot p mod 4 (planes beyond nz + 1 are never needed)
         auto issue = [&](int p, bool withhold = false) {
             if (p > nz + 1) return;
@@ -341,47 +381,49 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
             bool ok = true;
             const int z = wrap_coord(p, nz, a.per[2], ok);
             // failure-detection test: the phase of this fill can then never complete
-            if (withhold && tid == 0) return;
+            if (withhold && tid == waiter) return;
+            if (tid == waiter) s_hi_issued = p;
             if (tma) {
-                if (tid == 0) {
+                if (tid == waiter) {
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    mbar_expect_tx(&s_bar[slot], 3u * CAPS * 4u);
+                    // one arrival for the whole CTA, plus the bytes the copy delivers
+                    mbar_expect_tx_n(&s_bar[slot], 3u * CAPS * 4u, (unsigned)NT);
                     // an out-of-range plane of an open lattice: every element is zero-filled
-                    tma_load_4d(dst, map, xs, ys, ok ? z : -2, 0, &s_bar[slot]);
-                } else {
-                    mbar_arrive(&s_bar[slot]);
+                    tma_load_4d(dst, s_map, s_xs, s_ys, ok ? z : -2, 0, &s_bar[slot]);
                 }
             } else {
                 const int base = off + z * plane;
                 uint16_t *gd = sG + slot * CAPS;
 #pragma unroll
                 for (int l = 0; l < LPT; ++l) {
-                    if (lofs[l] == -2) continue;
                     const int idx = tid + l * NT;
-                    const bool v = ok && lofs[l] >= 0;
-                    const float *src = Sin + (v ? base + lofs[l] : 0);
+                    if (idx >= CAPS) continue;
+                    const int lofs = sL[idx];
+                    if (lofs == -2) continue;
+                    const bool v = ok && lofs >= 0;
+                    const float *src = Sin + (v ? base + lofs : 0);
                     cp_async4(dst + idx, src, v);
                     cp_async4(dst + CAPS + idx, src + NS, v);
                     cp_async4(dst + 2 * CAPS + idx, src + 2 * NS, v);
-                    if (mask) gd[idx] = v ? __ldg(a.gcode + base + lofs[l]) : (uint16_t)0;
+                    if (mask) gd[idx] = v ? __ldg(a.gcode + base + lofs) : (uint16_t)0;
                 }
                 mbar_arrive_cp_async(&s_bar[slot]);
             }
         };
-        // wait until plane p has landed in its slot; a wait that runs out is recorded here and
-        // acted on at the next barrier vote
+        // The waiter alone waits until plane p has landed in its slot (the other threads see the
+        // plane after the next barrier); a wait that runs out is recorded here and acted on at
+        // that barrier's vote.
         bool bad = false;
         auto await = [&](int p) {
             const int slot = (p + 4) & 3;
+            const int ph = s_ph;
             if (!mbar_wait(&s_bar[slot], (ph >> slot) & 1u, a.wait_polls)) {
                 bad = true;
                 atomicOr(&a.ctl->err, 2);
             }
-            ph ^= 1u << slot;
+            s_ph = ph ^ (1 << slot);
+            s_hi_waited = p;
         };
-
-        const float bapp = R.fB0 * field_polarity_f(R, a.bits, t);
-        const float bax = bapp * R.fdir[0], bay = bapp * R.fdir[1], baz = bapp * R.fdir[2];
         const unsigned site_plane = (unsigned)nx * (unsigned)ny;
 
         // prologue: planes -2 .. 1 staged; own S (and grain code) of planes -2 and -1 read
@@ -389,9 +431,13 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         issue(-1);
         issue(0);
         issue(1, a.inject && it == 0);
-        await(-2);
-        await(-1);
-        await(0);
+        if (tid == waiter) {
+            await(-2);
+            await(-1);
+            await(0);
+        }
+        // planes -2 .. 0 become visible to every thread
+        stop = __syncthreads_or(bad) != 0;
         float m1x[E], m1y[E], m1z[E];  // S on plane k-1 at each column
         float c0x[E], c0y[E], c0z[E];  // S on plane k
         unsigned gm1[E];               // grain code of plane k-1 (masked replicas)
@@ -416,15 +462,15 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                 c0z[j] = S3[2 * CAPS];
             }
         }
-        // plane -2's slot is restaged by the first march step; plain grain-code stores become visible
-        stop = __syncthreads_or(bad) != 0;
+        // plane -2's slot is restaged by the first march step
+        __syncthreads();
+        if (tid < nmarch) {
 
         // one march step; PH fixes the ring slots: plane k sits in slot (PH + 3) % 4
         auto march = [&](auto PHC, int k) {
             constexpr int PH = decltype(PHC)::value;
             constexpr int SK = (PH + 3) & 3, SK1 = PH & 3, SKM1 = (PH + 2) & 3, SKM2 = (PH + 1) & 3;
             issue(k + 3);  // into slot (k + 3) mod 4 = SKM1, left by plane k-1 (kept in registers)
-            if (k >= 0) await(k + 1);  // plane 0 was awaited by the prologue
             bool zok = true;
             const int wz = wrap_coord(k, nz, a.per[2], zok);
             float4 sp[E];       // S' of plane k (own, for the corrector's z+ neighbour)
@@ -450,9 +496,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                         normals3(philox10_rk(philox_ctr(scol[j] + site_plane * (unsigned)wz, (unsigned long long)step),
                                              s_rk),
                                  n0, n1, n2);
-                        hx[j] = fmaf(sig[j], n0, bax);
-                        hy[j] = fmaf(sig[j], n1, bay);
-                        hz[j] = fmaf(sig[j], n2, baz);
+                        const float4 ba = s_ba;
+                        hx[j] = fmaf(sig[j], n0, ba.x);
+                        hy[j] = fmaf(sig[j], n1, ba.y);
+                        hz[j] = fmaf(sig[j], n2, ba.z);
                         float3 B;
                         if constexpr (TET) {
                             B = field_s<TET, CAPS, SW>(a, make_float3(hx[j], hy[j], fmaf(a.cK, sz, hz[j])), P0, m1x[j],
@@ -493,7 +540,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                     sP[SK * CAPS + c[j]] = sp[j];
                 }
             }
-            stop = __syncthreads_or(bad) != 0;  // the step's one barrier, and the failure vote
+            // plane k+2 (read by the next step's predictor) is awaited by thread 0 before the
+            // step's one barrier, which also carries the failure vote
+            if (tid == waiter && k + 2 <= nz + 1) await(k + 2);
+            stop = bar_or(1, nmarch, bad);
             // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1) and k (own, sp)
             const int kc = k - 1;
             if (kc >= 0 && kc < nz) {
@@ -576,30 +626,29 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         };
 
         // k runs from -1 to nz; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
-        int kend = -2;  // last march step run
         for (int kb = -1; kb <= nz && !stop; kb += 4) {
             march(IC<0>(), kb);
-            kend = kb;
-            if (!stop && kb + 1 <= nz) march(IC<1>(), kend = kb + 1);
-            if (!stop && kb + 2 <= nz) march(IC<2>(), kend = kb + 2);
-            if (!stop && kb + 3 <= nz) march(IC<3>(), kend = kb + 3);
+            if (!stop && kb + 1 <= nz) march(IC<1>(), kb + 1);
+            if (!stop && kb + 2 <= nz) march(IC<2>(), kb + 2);
+            if (!stop && kb + 3 <= nz) march(IC<3>(), kb + 3);
         }
         if (stop) {
             // give the fills issued after the last awaited plane a bounded time to land before
             // the CTA's shared memory is released
-            if (tid == 0)
-                for (int p = max(kend + 2, 1); p <= min(kend + 3, nz + 1); ++p) {
+            if (tid == waiter)
+                for (int p = s_hi_waited + 1; p <= s_hi_issued; ++p) {
                     const int slot = (p + 4) & 3;
-                    mbar_wait(&s_bar[slot], (ph >> slot) & 1u, 1u << 22);
-                    ph ^= 1u << slot;
+                    mbar_wait(&s_bar[slot], (s_ph >> slot) & 1, 1u << 22);
+                    s_ph ^= 1 << slot;
                 }
-            return;  // uniform: every thread saw the same vote
-        }
-        if (RECORD) {
+        } else if (RECORD) {
 #pragma unroll
             for (int j = 0; j < E; ++j) grain_accumulate_fx(a.grain_fx, gacc[j], ax_[j], ay_[j], az_[j], gacc[j] >= 0);
         }
-        __syncthreads();  // all reads of this item's slots are done before they are re-armed
+        }  // marching warps
+        // all reads of this item's slots are done before they are re-armed; a failed wait ends
+        // the kernel for every thread
+        if (__syncthreads_or(stop)) return;
     }
 }
 
