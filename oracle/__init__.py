@@ -47,6 +47,17 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+class OrcMsParams(ctypes.Structure):
+    _fields_ = [
+        ("ncx", ctypes.c_int32), ("ncy", ctypes.c_int32), ("ncz", ctypes.c_int32),
+        ("cell", ctypes.c_double), ("ratio", ctypes.c_int32), ("wx", ctypes.c_int32),
+        ("J", ctypes.c_double), ("mu_s", ctypes.c_double), ("ku", ctypes.c_double),
+        ("Ms0", ctypes.c_double), ("A0", ctypes.c_double), ("K0", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("T_C", ctypes.c_double),
+        ("drv", OrcParams),
+    ]
+
+
 def _dp(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -88,6 +99,36 @@ def lib():
         L.orc_energy.restype = d
         L.orc_step_sites.argtypes = [P, vp, vp, i64, i64, vp, vp]
         L.orc_step_sites.restype = ctypes.c_int
+        # multiscale window (hamr_ms_oracle.c)
+        MP = ctypes.POINTER(OrcMsParams)
+        L.orc_langevin.argtypes = [d]
+        L.orc_langevin.restype = d
+        L.orc_me.argtypes = [d, d, d, d]
+        L.orc_me.restype = d
+        L.orc_theta_max.argtypes = [d]
+        L.orc_theta_max.restype = d
+        L.orc_ms_alpha.argtypes = [MP, d]
+        L.orc_ms_alpha.restype = d
+        L.orc_cone_sample.argtypes = [vp, d, u64, u64, u64, vp]
+        L.orc_ms_window_sites.argtypes = [MP]
+        L.orc_ms_window_sites.restype = i64
+        L.orc_ms_create.argtypes = [MP, vp]
+        L.orc_ms_create.restype = vp
+        L.orc_ms_destroy.argtypes = [vp]
+        L.orc_ms_set_cells.argtypes = [vp, vp]
+        L.orc_ms_get_cells.argtypes = [vp, vp]
+        L.orc_ms_get_moments.argtypes = [vp, vp]
+        L.orc_ms_set_moments.argtypes = [vp, vp]
+        L.orc_ms_window.argtypes = [vp]
+        L.orc_ms_window.restype = i32
+        L.orc_ms_step_count.argtypes = [vp]
+        L.orc_ms_step_count.restype = i64
+        L.orc_ms_set_window.argtypes = [vp, i32]
+        L.orc_ms_set_window.restype = ctypes.c_int
+        L.orc_ms_target.argtypes = [MP, d]
+        L.orc_ms_target.restype = i32
+        L.orc_ms_run.argtypes = [vp, i64, i32]
+        L.orc_ms_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -282,3 +323,142 @@ def step_sites(p, grain, S, step, sites):
     if rc != 0:
         raise RuntimeError("oracle neighbour list overflow")
     return out
+
+
+# --------------------------------------------------------------------------- multiscale window
+def langevin(x):
+    """L(x) = coth x - 1/x (Sec. II)."""
+    return lib().orc_langevin(float(x))
+
+
+def me(T_C, T, mu_s, B):
+    """Equilibrium magnetisation m_e(T): the root of m = L(3 T_C m / T + mu_s B / kB T)."""
+    return lib().orc_me(float(T_C), float(T), float(mu_s), float(B))
+
+
+def theta_max(mr):
+    """Half-angle of the thermalisation cone for M / Ms0 = mr (Sec. II)."""
+    return lib().orc_theta_max(float(mr))
+
+
+def cone_sample(e3, th_max, seed, site, event):
+    out = np.zeros(3)
+    e3 = np.ascontiguousarray(e3, dtype=np.float64)
+    lib().orc_cone_sample(_dp(e3), float(th_max), int(seed), int(site), int(event), _dp(out))
+    return out
+
+
+class MsParams:
+    """Multiscale window: ncx x ncy x ncz micromagnetic cells of edge `cell`, an atomistic
+    simple-cubic window of spacing cell/ratio covering wx cell columns (all of y and z).
+    The micromagnetic constants default to the atomistic ones per unit volume: Ms0 =
+    mu_s / a^3, K0 = ku / a^3 (Appendix A) and A0 = J / 2a (Eq. 9)."""
+
+    def __init__(self, ncx, ncy, ncz, cell, ratio, wx, *, J, mu_s=3 * C_MU_B, ku=0.0, lam=0.1,
+                 T_C=None, Ms0=None, A0=None, K0=None, dt=1e-16, gamma=C_GAMMA, seed=1,
+                 T_amb=0.0, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0,
+                 B0=0.0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0, ramp_len=0.0,
+                 head_x0=0.0, head_v=0.0):
+        self.ncx, self.ncy, self.ncz = int(ncx), int(ncy), int(ncz)
+        self.cell, self.ratio, self.wx = float(cell), int(ratio), int(wx)
+        a = self.cell / self.ratio
+        self.a = a
+        self.J, self.mu_s, self.ku, self.lam = J, mu_s, ku, lam
+        self.T_C = 1.443 * J / C_KB if T_C is None else T_C
+        self.Ms0 = mu_s / a ** 3 if Ms0 is None else Ms0
+        self.A0 = J / (2 * a) if A0 is None else A0
+        self.K0 = ku / a ** 3 if K0 is None else K0
+        # the drivers, time step, gyromagnetic ratio and seed ride in an atomistic Params
+        self.drv = Params(1, 1, 1, (a, a, a), (a,), (J,), mu_s=mu_s, ku=ku, alpha=lam, dt=dt,
+                          gamma=gamma, seed=seed, T_amb=T_amb, T_peak=T_peak, fwhm=fwhm, x0=x0,
+                          y0=y0, vx=vx, vy=vy, B0=B0, direction=direction, bits=bits,
+                          bit_len=bit_len, ramp_len=ramp_len, head_x0=head_x0, head_v=head_v)
+
+    @property
+    def n_cells(self):
+        return self.ncx * self.ncy * self.ncz
+
+    @property
+    def window_dims(self):
+        r = self.ratio
+        return (self.wx * r, self.ncy * r, self.ncz * r)
+
+    def struct(self):
+        s = OrcMsParams()
+        s.ncx, s.ncy, s.ncz = self.ncx, self.ncy, self.ncz
+        s.cell, s.ratio, s.wx = self.cell, self.ratio, self.wx
+        s.J, s.mu_s, s.ku = self.J, self.mu_s, self.ku
+        s.Ms0, s.A0, s.K0 = self.Ms0, self.A0, self.K0
+        s.lambda_, s.T_C = self.lam, self.T_C
+        s.drv = self.drv.struct()
+        self._keep = self.drv
+        return s
+
+
+def ms_alpha(p, T):
+    s = p.struct()
+    return lib().orc_ms_alpha(ctypes.byref(s), float(T))
+
+
+def ms_target(p, t):
+    s = p.struct()
+    return lib().orc_ms_target(ctypes.byref(s), float(t))
+
+
+class MsOracle:
+    """The multiscale window on the CPU: cells' grain ids (int32, -1 = non-magnetic),
+    micromagnetic directions m (n_cells, 3) and the window spins S (n_window, 3)."""
+
+    def __init__(self, p, cell_grain=None):
+        self.p = p
+        self._s = p.struct()
+        if cell_grain is None:
+            cell_grain = np.zeros(p.n_cells, dtype=np.int32)
+        self.grain = np.ascontiguousarray(cell_grain, dtype=np.int32).reshape(-1)
+        assert self.grain.size == p.n_cells
+        self._h = lib().orc_ms_create(ctypes.byref(self._s), _dp(self.grain))
+        if not self._h:
+            raise MemoryError("oracle context allocation failed")
+        self.nw = int(np.prod(p.window_dims))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_ms_destroy(h)
+            self._h = None
+
+    def set_cells(self, m):
+        m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1)
+        assert m.size == 3 * self.p.n_cells
+        lib().orc_ms_set_cells(self._h, _dp(m))
+
+    def cells(self):
+        m = np.zeros((self.p.n_cells, 3))
+        lib().orc_ms_get_cells(self._h, _dp(m))
+        return m
+
+    def moments(self):
+        S = np.zeros((self.nw, 3))
+        lib().orc_ms_get_moments(self._h, _dp(S))
+        return S
+
+    def set_moments(self, S):
+        S = np.ascontiguousarray(S, dtype=np.float64).reshape(-1)
+        assert S.size == 3 * self.nw
+        lib().orc_ms_set_moments(self._h, _dp(S))
+
+    @property
+    def window(self):
+        return lib().orc_ms_window(self._h)
+
+    @property
+    def step(self):
+        return lib().orc_ms_step_count(self._h)
+
+    def set_window(self, ox):
+        if lib().orc_ms_set_window(self._h, int(ox)) != 0:
+            raise ValueError("window outside the track")
+
+    def run(self, n_steps, follow=False):
+        if lib().orc_ms_run(self._h, int(n_steps), int(bool(follow))) != 0:
+            raise MemoryError("oracle step allocation failed")

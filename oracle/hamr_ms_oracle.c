@@ -1,0 +1,489 @@
+/*
+ * hamr_ms_oracle.c -- plain FP64 CPU oracle for the multiscale window of the paper
+ * (Sec. II and Fig. 1): a simple-cubic atomistic window embedded in a micromagnetic
+ * finite-difference track, exchange coupled across the interface and moving with the
+ * laser spot.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's
+ * CPU baseline may load it.  It shares no code, header, table or constant with the CUDA
+ * library.
+ *
+ * Geometry.  The track is ncx x ncy x ncz cubic cells of edge `cell`.  The atomistic
+ * lattice has spacing a = cell / ratio, so each cell holds ratio^3 sites.  The window is
+ * wx cells long, starts at cell column ox and spans every cell in y and z.  A cell's grain
+ * id (-1 = non-magnetic) is shared by every site inside it.
+ *
+ * One coupled step n -> n+1 (t_n = n dt).  Drivers (laser temperature, write field) are
+ * frozen at t_n for the whole step.
+ *   1. Eq. 6: each cell inside the window takes the direction of the sum of its
+ *      atomistic spins (0 for a non-magnetic cell).  The micromagnetic exchange of the
+ *      neighbouring cells then sees the average atomistic direction (Sec. II).
+ *   2. The atomistic sLLG Heun step of the window (Eq. 1-3, thermal field as in
+ *      hamr_oracle.c, counter = the site's index on the whole track).  A site whose
+ *      x-neighbour lies outside the window takes, for that bond, the direction of the
+ *      micromagnetic cell containing the neighbour (Eq. 2 with the cell's m, Sec. II).
+ *      Bonds join only sites (or a site and a cell) of the same grain.
+ *   3. One classical RK4 step of the micromagnetic LLG (Eq. 1 without the thermal field)
+ *      on every magnetic cell outside the window, with
+ *        B = (2 A(T) / Ms(T)) lap(m) + (2 K(T) / Ms(T)) (m.z) z + B_app        (Eq. 4, 5)
+ *      where lap is the 6-neighbour finite-difference Laplacian over same-grain magnetic
+ *      neighbours (a missing neighbour adds nothing), Ms(T) = Ms0 m_e, A(T) = A0 m_e^2,
+ *      K(T) = K0 m_e^3, damping alpha(T) = lambda (1 - T / 3 T_C) with T capped at T_C,
+ *      and m_e(T) the root of m = L(3 T_C m / T + mu_s |B_app| / (kB T)) with the
+ *      Langevin function L(x) = coth x - 1/x (Sec. II).  Cells inside the window are
+ *      frozen at their Eq. 6 directions.  m is renormalised after the step.
+ *   4. If the window follows the laser, it is moved forward one cell column at a time
+ *      until it is centred on the spot (Sec. II, Fig. 1): the trailing column is handed to
+ *      the micromagnetic side by Eq. 6, the sites shift back by `ratio`, and the new
+ *      leading column is thermalised: every site gets a spin whose polar angle from the
+ *      cell's m is uniform in [0, theta_max] and whose azimuth is uniform, with
+ *      theta_max = (5 pi / 9) sqrt(1 - sqrt(1 + 6 (M/Ms0 - 1) / 5)) and M/Ms0 = m_e(T) of
+ *      the cell (the square root's argument is kept in [0, 1]).
+ */
+#include "hamr_oracle.h"
+
+typedef struct {
+    int32_t ncx, ncy, ncz;  /* micromagnetic cells */
+    double cell;            /* cell edge [m] */
+    int32_t ratio;          /* atomistic sites per cell edge */
+    int32_t wx;             /* window length in cells */
+    double J, mu_s, ku;     /* atomistic exchange [J], moment [J/T], anisotropy per atom [J] */
+    double Ms0, A0, K0;     /* micromagnetic Ms [A/m], A [J/m], K [J/m^3] at 0 K */
+    double lambda;          /* atomistic damping; micromagnetic alpha(T) = lambda (1 - T/3T_C) */
+    double T_C;             /* Curie temperature [K] */
+    orc_params drv;         /* gamma, dt, seed, laser spot and write field (other fields unused) */
+} orc_ms_params;
+
+typedef struct {
+    orc_ms_params p;
+    uint8_t *bits;
+    int64_t nc;             /* cells */
+    int32_t *grain;         /* [nc] */
+    double *m;              /* [3 nc] AoS; window cells hold their Eq. 6 directions */
+    int32_t ox;             /* first cell column of the window */
+    int64_t nw;             /* sites in the window */
+    double *S;              /* [3 nw] AoS, site (i, j, k) at i + nxw (j + nyw k) */
+    int64_t step;           /* completed steps */
+    int64_t events;         /* thermalisation events so far (window placements and moves) */
+} orc_ms;
+
+/* ------------------------------------------------------------------------- */
+/* Temperature dependence of the micromagnetic parameters (Sec. II) */
+
+/* Langevin function coth x - 1/x; its series x/3 - x^3/45 + 2x^5/945 near 0. */
+double orc_langevin(double x)
+{
+    if (fabs(x) < 1e-3) return x / 3.0 - x * x * x / 45.0 + 2.0 * x * x * x * x * x / 945.0;
+    return 1.0 / tanh(x) - 1.0 / x;
+}
+
+/* m_e(T): the largest root in [0, 1] of m = L(3 T_C m / T + mu_s B / (kB T)), by
+ * bisection on the sign of L(...) - m (m_e = 1 at T <= 0). */
+double orc_me(double T_C, double T, double mu_s, double B)
+{
+    if (!(T > 0.0)) return 1.0;
+    double a = 3.0 * T_C / T, b = mu_s * B / (ORC_KB * T);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_langevin(a * mid + b) - mid >= 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+double orc_ms_alpha(const orc_ms_params *p, double T)
+{
+    double Tc = T < p->T_C ? T : p->T_C;
+    if (Tc < 0.0) Tc = 0.0;
+    return p->lambda * (1.0 - Tc / (3.0 * p->T_C));
+}
+
+/* The cone half-angle of the thermalisation rule for M / Ms0 = mr. */
+double orc_theta_max(double mr)
+{
+    double x = 1.0 + 6.0 * (mr - 1.0) / 5.0;
+    if (x < 0.0) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    return (5.0 * ORC_PI / 9.0) * sqrt(1.0 - sqrt(x));
+}
+
+/* A unit spin in the cone of half-angle theta_max around the unit vector e3: polar angle
+ * theta = u0 theta_max, azimuth phi = 2 pi u1 about e3, measured from
+ * e1 = (z x e3)/|z x e3| (or (x x e3)/|x x e3| when |e3_z| >= 0.9), e2 = e3 x e1; u0 and
+ * u1 are the first two words of Philox4x32-10 with key (seed low, seed high) and counter
+ * (site low, site high, event low, event high | 2^31), mapped to (x + 1/2) 2^-32. */
+void orc_cone_sample(const double e3[3], double theta_max, uint64_t seed, uint64_t site, uint64_t event,
+                     double out[3])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)site, (uint32_t)(site >> 32), (uint32_t)event,
+                       (uint32_t)(event >> 32) | 0x80000000u};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    double u0 = ((double)x[0] + 0.5) * (1.0 / 4294967296.0);
+    double u1 = ((double)x[1] + 0.5) * (1.0 / 4294967296.0);
+    double th = u0 * theta_max, ph = 2.0 * ORC_PI * u1;
+    double e1[3];
+    if (fabs(e3[2]) < 0.9) {
+        e1[0] = -e3[1]; e1[1] = e3[0]; e1[2] = 0.0;            /* z x e3 */
+    } else {
+        e1[0] = 0.0; e1[1] = -e3[2]; e1[2] = e3[1];            /* x x e3 */
+    }
+    double r = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int d = 0; d < 3; ++d) e1[d] /= r;
+    double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2], e3[0] * e1[1] - e3[1] * e1[0]};
+    double a1 = sin(th) * cos(ph), a2 = sin(th) * sin(ph), a3 = cos(th);
+    for (int d = 0; d < 3; ++d) out[d] = a1 * e1[d] + a2 * e2[d] + a3 * e3[d];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Context */
+
+static int64_t cell_index(const orc_ms_params *p, int64_t cx, int64_t cy, int64_t cz)
+{
+    return cx + (int64_t)p->ncx * (cy + (int64_t)p->ncy * cz);
+}
+
+int64_t orc_ms_window_sites(const orc_ms_params *p)
+{
+    return (int64_t)p->wx * p->ratio * (int64_t)p->ncy * p->ratio * (int64_t)p->ncz * p->ratio;
+}
+
+void orc_ms_destroy(orc_ms *c)
+{
+    if (!c) return;
+    free(c->bits); free(c->grain); free(c->m); free(c->S);
+    free(c);
+}
+
+orc_ms *orc_ms_create(const orc_ms_params *p, const int32_t *cell_grain)
+{
+    orc_ms *c = (orc_ms *)calloc(1, sizeof(orc_ms));
+    if (!c) return NULL;
+    c->p = *p;
+    if (p->drv.n_bits > 0) {
+        c->bits = (uint8_t *)malloc((size_t)p->drv.n_bits);
+        memcpy(c->bits, p->drv.bits, (size_t)p->drv.n_bits);
+        c->p.drv.bits = c->bits;
+    }
+    c->nc = (int64_t)p->ncx * p->ncy * p->ncz;
+    c->grain = (int32_t *)malloc(sizeof(int32_t) * (size_t)c->nc);
+    memcpy(c->grain, cell_grain, sizeof(int32_t) * (size_t)c->nc);
+    c->m = (double *)calloc(3 * (size_t)c->nc, sizeof(double));
+    c->nw = orc_ms_window_sites(p);
+    c->S = (double *)calloc(3 * (size_t)c->nw, sizeof(double));
+    return c;
+}
+
+void orc_ms_set_cells(orc_ms *c, const double *m)
+{
+    for (int64_t q = 0; q < c->nc; ++q)
+        for (int d = 0; d < 3; ++d) c->m[3 * q + d] = c->grain[q] >= 0 ? m[3 * q + d] : 0.0;
+}
+
+void orc_ms_get_cells(const orc_ms *c, double *m) { memcpy(m, c->m, sizeof(double) * 3 * (size_t)c->nc); }
+void orc_ms_get_moments(const orc_ms *c, double *S) { memcpy(S, c->S, sizeof(double) * 3 * (size_t)c->nw); }
+void orc_ms_set_moments(orc_ms *c, const double *S) { memcpy(c->S, S, sizeof(double) * 3 * (size_t)c->nw); }
+int32_t orc_ms_window(const orc_ms *c) { return c->ox; }
+int64_t orc_ms_step_count(const orc_ms *c) { return c->step; }
+
+/* Site (i, j, k) of the window: its cell, grain and index on the whole track. */
+static int64_t site_cell(const orc_ms *c, int64_t i, int64_t j, int64_t k)
+{
+    const int r = c->p.ratio;
+    return cell_index(&c->p, c->ox + i / r, j / r, k / r);
+}
+
+static uint64_t track_site(const orc_ms *c, int64_t i, int64_t j, int64_t k)
+{
+    const int64_t r = c->p.ratio;
+    const int64_t X = (int64_t)c->ox * r + i, NX = (int64_t)c->p.ncx * r, NY = (int64_t)c->p.ncy * r;
+    return (uint64_t)(X + NX * (j + NY * k));
+}
+
+/* Eq. 6 for the window cells of columns [cx0, cx1): the direction of the sum of the
+ * cell's atomistic spins (0 for a non-magnetic cell or a zero sum). */
+static void average_cells(orc_ms *c, int32_t cx0, int32_t cx1)
+{
+    const int r = c->p.ratio;
+    const int64_t nxw = (int64_t)c->p.wx * r, nyw = (int64_t)c->p.ncy * r;
+    for (int32_t cz = 0; cz < c->p.ncz; ++cz)
+        for (int32_t cy = 0; cy < c->p.ncy; ++cy)
+            for (int32_t cx = cx0; cx < cx1; ++cx) {
+                int64_t q = cell_index(&c->p, cx, cy, cz);
+                double s[3] = {0.0, 0.0, 0.0};
+                if (c->grain[q] >= 0)
+                    for (int dk = 0; dk < r; ++dk)
+                        for (int dj = 0; dj < r; ++dj)
+                            for (int di = 0; di < r; ++di) {
+                                int64_t i = (int64_t)(cx - c->ox) * r + di, j = (int64_t)cy * r + dj,
+                                        k = (int64_t)cz * r + dk;
+                                const double *Si = c->S + 3 * (i + nxw * (j + nyw * k));
+                                for (int d = 0; d < 3; ++d) s[d] += Si[d];
+                            }
+                double n = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+                for (int d = 0; d < 3; ++d) c->m[3 * q + d] = n > 0.0 ? s[d] / n : 0.0;
+            }
+}
+
+static double cell_temperature(const orc_ms *c, int64_t q, double t)
+{
+    int64_t cx = q % c->p.ncx, cy = (q / c->p.ncx) % c->p.ncy;
+    return orc_temperature(&c->p.drv, (cx + 0.5) * c->p.cell, (cy + 0.5) * c->p.cell, t);
+}
+
+/* Thermalise the window sites of cell columns [cx0, cx1) from the cells' m (event index
+ * `event` in the Philox counter). */
+static void thermalise(orc_ms *c, int32_t cx0, int32_t cx1, double t, uint64_t event)
+{
+    const int r = c->p.ratio;
+    const int64_t nxw = (int64_t)c->p.wx * r, nyw = (int64_t)c->p.ncy * r, nzw = (int64_t)c->p.ncz * r;
+    double B[3];
+    orc_applied_field(&c->p.drv, t, B);
+    double Bm = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    for (int64_t k = 0; k < nzw; ++k)
+        for (int64_t j = 0; j < nyw; ++j)
+            for (int64_t i = (int64_t)(cx0 - c->ox) * r; i < (int64_t)(cx1 - c->ox) * r; ++i) {
+                int64_t q = site_cell(c, i, j, k);
+                double *Si = c->S + 3 * (i + nxw * (j + nyw * k));
+                const double *mq = c->m + 3 * q;
+                if (c->grain[q] < 0 || (mq[0] == 0.0 && mq[1] == 0.0 && mq[2] == 0.0)) {
+                    Si[0] = Si[1] = Si[2] = 0.0;
+                    continue;
+                }
+                double mr = orc_me(c->p.T_C, cell_temperature(c, q, t), c->p.mu_s, Bm);
+                orc_cone_sample(mq, orc_theta_max(mr), c->p.drv.seed, track_site(c, i, j, k), event, Si);
+            }
+}
+
+/* Place the window at cell column ox and thermalise all of it from the cells. */
+int orc_ms_set_window(orc_ms *c, int32_t ox)
+{
+    if (ox < 0 || ox + c->p.wx > c->p.ncx) return -1;
+    c->ox = ox;
+    thermalise(c, ox, ox + c->p.wx, (double)c->step * c->p.drv.dt, (uint64_t)c->events);
+    c->events += 1;
+    return 0;
+}
+
+/* Move the window forward by one cell column (step 4 of the header). */
+static void shift_forward(orc_ms *c, double t)
+{
+    const int r = c->p.ratio;
+    const int64_t nxw = (int64_t)c->p.wx * r, nyw = (int64_t)c->p.ncy * r, nzw = (int64_t)c->p.ncz * r;
+    average_cells(c, c->ox, c->ox + 1);
+    for (int64_t k = 0; k < nzw; ++k)
+        for (int64_t j = 0; j < nyw; ++j)
+            for (int64_t i = 0; i + r < nxw; ++i)
+                for (int d = 0; d < 3; ++d)
+                    c->S[3 * (i + nxw * (j + nyw * k)) + d] = c->S[3 * (i + r + nxw * (j + nyw * k)) + d];
+    c->ox += 1;
+    thermalise(c, c->ox + c->p.wx - 1, c->ox + c->p.wx, t, (uint64_t)c->events);
+    c->events += 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Atomistic step of the window (stage 2) */
+
+/* Exchange sum sum_j J S_j of site (i, j, k) over its same-grain bonds, with the window
+ * spins V and, across the window's x faces, the micromagnetic cells m. */
+static void site_exchange(const orc_ms *c, const double *V, int64_t i, int64_t j, int64_t k, int32_t g,
+                          double ex[3])
+{
+    const int r = c->p.ratio;
+    const int64_t nxw = (int64_t)c->p.wx * r, nyw = (int64_t)c->p.ncy * r, nzw = (int64_t)c->p.ncz * r;
+    ex[0] = ex[1] = ex[2] = 0.0;
+    const int64_t off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (int b = 0; b < 6; ++b) {
+        int64_t ii = i + off[b][0], jj = j + off[b][1], kk = k + off[b][2];
+        if (jj < 0 || jj >= nyw || kk < 0 || kk >= nzw) continue;
+        const double *v;
+        int32_t gj;
+        if (ii >= 0 && ii < nxw) {
+            gj = c->grain[site_cell(c, ii, jj, kk)];
+            v = V + 3 * (ii + nxw * (jj + nyw * kk));
+        } else {
+            int64_t cx = c->ox + (ii < 0 ? -1 : c->p.wx);
+            if (cx < 0 || cx >= c->p.ncx) continue;
+            int64_t q = cell_index(&c->p, cx, jj / r, kk / r);
+            gj = c->grain[q];
+            v = c->m + 3 * q;
+        }
+        if (gj != g) continue;
+        for (int d = 0; d < 3; ++d) ex[d] += c->p.J * v[d];
+    }
+}
+
+static void atom_rhs(const orc_ms *c, const double S[3], const double B[3], double f[3])
+{
+    orc_params q = c->p.drv;
+    q.alpha = c->p.lambda;
+    orc_llg_rhs(&q, S, B, f);
+}
+
+static int atom_step(orc_ms *c)
+{
+    const orc_ms_params *p = &c->p;
+    const int r = p->ratio;
+    const int64_t nxw = (int64_t)p->wx * r, nyw = (int64_t)p->ncy * r, nzw = (int64_t)p->ncz * r;
+    const int64_t n = c->nw;
+    const double dt = p->drv.dt, t = (double)c->step * dt, a = p->cell / r;
+    double *Bth = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *f1 = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *Sp = (double *)calloc(3 * (size_t)n, sizeof(double));
+    if (!Bth || !f1 || !Sp) { free(Bth); free(f1); free(Sp); return -1; }
+    double Bapp[3];
+    orc_applied_field(&p->drv, t, Bapp);
+    /* thermal field, field at S and predictor */
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n; ++s) {
+        int64_t i = s % nxw, j = (s / nxw) % nyw, k = s / (nxw * nyw);
+        int32_t g = c->grain[site_cell(c, i, j, k)];
+        if (g < 0) continue;
+        double T = orc_temperature(&p->drv, ((double)c->ox * r + i + 0.5) * a, (j + 0.5) * a, t);
+        double sigma = sqrt(2.0 * p->lambda * ORC_KB * T / (p->drv.gamma * p->mu_s * dt));
+        double xi[3];
+        orc_thermal_normals(p->drv.seed, track_site(c, i, j, k), (uint64_t)c->step, xi);
+        for (int d = 0; d < 3; ++d) Bth[3 * s + d] = sigma * xi[d];
+        double ex[3], B[3];
+        site_exchange(c, c->S, i, j, k, g, ex);
+        const double *Si = c->S + 3 * s;
+        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
+        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1];
+        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2];
+        atom_rhs(c, Si, B, f1 + 3 * s);
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = Si[d] + dt * f1[3 * s + d];
+        double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int d = 0; d < 3; ++d) Sp[3 * s + d] = v[d] / nv;
+    }
+    /* field at S' and corrector */
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n; ++s) {
+        int64_t i = s % nxw, j = (s / nxw) % nyw, k = s / (nxw * nyw);
+        int32_t g = c->grain[site_cell(c, i, j, k)];
+        if (g < 0) continue;
+        double ex[3], B[3], f2[3];
+        site_exchange(c, Sp, i, j, k, g, ex);
+        const double *Spi = Sp + 3 * s;
+        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
+        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1];
+        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Spi[2] + Bapp[2] + Bth[3 * s + 2];
+        atom_rhs(c, Spi, B, f2);
+        double *Si = c->S + 3 * s;
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = Si[d] + 0.5 * dt * (f1[3 * s + d] + f2[d]);
+        double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int d = 0; d < 3; ++d) Si[d] = v[d] / nv;
+    }
+    free(Bth); free(f1); free(Sp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Micromagnetic RK4 step (stage 3) */
+
+/* dm/dt of cell q for the stage values V, with per-cell m_e and T at t_n. */
+static void mm_rate(const orc_ms *c, const double *V, int64_t q, double me, double T, const double Bapp[3],
+                    double k[3])
+{
+    const orc_ms_params *p = &c->p;
+    int64_t cx = q % p->ncx, cy = (q / p->ncx) % p->ncy, cz = q / ((int64_t)p->ncx * p->ncy);
+    const int64_t off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    const double *mq = V + 3 * q;
+    double lap[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 6; ++b) {
+        int64_t x = cx + off[b][0], y = cy + off[b][1], z = cz + off[b][2];
+        if (x < 0 || x >= p->ncx || y < 0 || y >= p->ncy || z < 0 || z >= p->ncz) continue;
+        int64_t qn = cell_index(p, x, y, z);
+        if (c->grain[qn] != c->grain[q]) continue;
+        for (int d = 0; d < 3; ++d) lap[d] += (V[3 * qn + d] - mq[d]) / (p->cell * p->cell);
+    }
+    double cex = 2.0 * p->A0 * me * me / (p->Ms0 * me), cK = 2.0 * p->K0 * me * me * me / (p->Ms0 * me);
+    if (!(me > 0.0)) cex = cK = 0.0;
+    double B[3] = {cex * lap[0] + Bapp[0], cex * lap[1] + Bapp[1], cex * lap[2] + cK * mq[2] + Bapp[2]};
+    orc_params pp = p->drv;
+    pp.alpha = orc_ms_alpha(p, T);
+    orc_llg_rhs(&pp, mq, B, k);
+}
+
+static int mm_step(orc_ms *c)
+{
+    const orc_ms_params *p = &c->p;
+    const int64_t nc = c->nc;
+    const double dt = p->drv.dt, t = (double)c->step * dt;
+    double *V = (double *)malloc(sizeof(double) * 3 * (size_t)nc);
+    double *K = (double *)malloc(sizeof(double) * 3 * (size_t)nc);
+    double *acc = (double *)calloc(3 * (size_t)nc, sizeof(double));
+    double *me = (double *)malloc(sizeof(double) * (size_t)nc);
+    double *T = (double *)malloc(sizeof(double) * (size_t)nc);
+    if (!V || !K || !acc || !me || !T) { free(V); free(K); free(acc); free(me); free(T); return -1; }
+    double Bapp[3];
+    orc_applied_field(&p->drv, t, Bapp);
+    double Bm = sqrt(Bapp[0] * Bapp[0] + Bapp[1] * Bapp[1] + Bapp[2] * Bapp[2]);
+    for (int64_t q = 0; q < nc; ++q) {
+        T[q] = cell_temperature(c, q, t);
+        me[q] = orc_me(p->T_C, T[q], p->mu_s, Bm);
+    }
+#define ORC_EVOLVED(q) (c->grain[q] >= 0 && ((q) % p->ncx < c->ox || (q) % p->ncx >= c->ox + p->wx))
+    memcpy(V, c->m, sizeof(double) * 3 * (size_t)nc);
+    const double cstage[4] = {0.5, 0.5, 1.0, 0.0}, wstage[4] = {1.0, 2.0, 2.0, 1.0};
+    for (int s = 0; s < 4; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < nc; ++q) {
+            if (!ORC_EVOLVED(q)) continue;
+            mm_rate(c, V, q, me[q], T[q], Bapp, K + 3 * q);
+        }
+        for (int64_t q = 0; q < nc; ++q) {
+            if (!ORC_EVOLVED(q)) continue;
+            for (int d = 0; d < 3; ++d) {
+                acc[3 * q + d] += wstage[s] * K[3 * q + d];
+                V[3 * q + d] = c->m[3 * q + d] + cstage[s] * dt * K[3 * q + d];
+            }
+        }
+    }
+    for (int64_t q = 0; q < nc; ++q) {
+        if (!ORC_EVOLVED(q)) continue;
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = c->m[3 * q + d] + dt / 6.0 * acc[3 * q + d];
+        double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int d = 0; d < 3; ++d) c->m[3 * q + d] = v[d] / nv;
+    }
+#undef ORC_EVOLVED
+    free(V); free(K); free(acc); free(me); free(T);
+    return 0;
+}
+
+/* The window's target column: centred on the laser spot at time t, within the track. */
+int32_t orc_ms_target(const orc_ms_params *p, double t)
+{
+    double xc = p->drv.x0 + p->drv.vx * t;
+    double f = floor(xc / p->cell - 0.5 * p->wx + 0.5);
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(p->ncx - p->wx)) f = (double)(p->ncx - p->wx);
+    return (int32_t)f;
+}
+
+/* n_steps coupled steps (stages 1-4 of the header); follow != 0 moves the window with the
+ * laser spot after each step.  Returns 0, or -1 on allocation failure. */
+int orc_ms_run(orc_ms *c, int64_t n_steps, int32_t follow)
+{
+    for (int64_t s = 0; s < n_steps; ++s) {
+        average_cells(c, c->ox, c->ox + c->p.wx);
+        if (atom_step(c) != 0) return -1;
+        if (mm_step(c) != 0) return -1;
+        c->step += 1;
+        if (follow) {
+            double t = (double)c->step * c->p.drv.dt;
+            int32_t target = orc_ms_target(&c->p, t);
+            while (c->ox < target) shift_forward(c, t);
+        }
+    }
+    /* the window cells report the Eq. 6 directions of the current spins */
+    average_cells(c, c->ox, c->ox + c->p.wx);
+    return 0;
+}

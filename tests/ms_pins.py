@@ -1,0 +1,342 @@
+"""Pins of the multiscale-window oracle (oracle/hamr_ms_oracle.c) to what the paper and the
+mathematics fix: limits of the equilibrium magnetisation m_e(T), the printed values of the
+thermalisation cone law, the cone's polar-angle distribution, Eq. 6 by brute force, the
+micromagnetic LLG in closed form for an isolated cell, and the equivalence of the
+micromagnetic and atomistic equations of motion when a cell holds one site (Eq. 9).
+Sections and equations refer to arXiv 2502.02236.
+"""
+import math
+
+import numpy as np
+
+import oracle as o
+
+A = 0.25e-9
+MU_S = 3 * o.C_MU_B
+J_SC = 6.7e-21
+KU = 1.0e-22
+G = o.C_GAMMA
+KB = o.C_KB
+
+
+# ----------------------------------------------------------------------------- m_e(T)
+def check_langevin_branches():
+    """L(x) = coth x - 1/x: the small-x series and the closed form agree where they meet,
+    L is odd, and L(x) -> 1 - 1/x for large x."""
+    for x in (9.99e-4, 1.001e-3):
+        assert abs(o.langevin(x) - (1 / math.tanh(x) - 1 / x)) < 1e-12
+        assert abs(o.langevin(x) - x / 3) < x ** 3 / 40
+    assert o.langevin(-0.7) == -o.langevin(0.7)
+    assert abs(o.langevin(50.0) - (1 - 1 / 50.0)) < 1e-15
+
+
+def check_me_limits():
+    """m_e(T) (Sec. II): 1 at T -> 0 with the low-temperature slope 1 - T/3T_C; 0 above T_C
+    without a field; the mean-field critical law m_e^2 = (5/3)(T_C/T - 1)(T/T_C)^3 just
+    below T_C; the Curie-Weiss response (mu_s B / 3 kB T) / (1 - T_C/T) well above T_C."""
+    Tc = 700.0
+    assert o.me(Tc, 0.0, MU_S, 0.0) == 1.0
+    for T in (1.0, 5.0):
+        assert abs(o.me(Tc, T, MU_S, 0.0) - (1 - T / (3 * Tc))) < 2 * (T / Tc) ** 2
+    # at T_C the residual is cubic in m, so bisection stops near 1e-8
+    assert o.me(Tc, Tc, MU_S, 0.0) < 1e-6
+    for T in (1.2 * Tc, 3 * Tc):
+        assert o.me(Tc, T, MU_S, 0.0) < 1e-12
+    T = 0.999 * Tc
+    want = math.sqrt(5.0 / 3.0 * (Tc / T - 1) * (T / Tc) ** 3)
+    assert abs(o.me(Tc, T, MU_S, 0.0) / want - 1) < 5e-3
+    T, B = 4 * Tc, 1.0
+    cw = (MU_S * B / (3 * KB * T)) / (1 - Tc / T)
+    assert abs(o.me(Tc, T, MU_S, B) / cw - 1) < 1e-3
+    # a field raises m_e; heating lowers it
+    assert o.me(Tc, 500.0, MU_S, 2.0) > o.me(Tc, 500.0, MU_S, 0.0) > o.me(Tc, 600.0, MU_S, 0.0)
+
+
+def check_micromagnetic_damping_law():
+    """alpha(T) = lambda (1 - T / 3 T_C) below T_C (Sec. II): lambda at 0 K, 2 lambda / 3 at T_C."""
+    p = o.MsParams(4, 1, 1, A, 1, 1, J=J_SC, lam=0.1)
+    assert o.ms_alpha(p, 0.0) == 0.1
+    assert abs(o.ms_alpha(p, p.T_C) - 0.2 / 3) < 1e-15
+    assert abs(o.ms_alpha(p, 0.5 * p.T_C) - 0.1 * (1 - 1 / 6)) < 1e-15
+
+
+# ----------------------------------------------------------------------------- thermalisation
+def check_theta_max_printed_values():
+    """theta_max = (5 pi / 9) sqrt(1 - sqrt(1 + 6 (M/Ms0 - 1)/5)) (Sec. II): 0 for a fully
+    ordered cell, 5 pi / 9 at M/Ms0 = 1/6 where the inner root vanishes, and decreasing in
+    between; below 1/6 the root's argument is held at 0."""
+    assert o.theta_max(1.0) == 0.0
+    assert abs(o.theta_max(1 / 6) - 5 * math.pi / 9) < 1e-15
+    assert o.theta_max(0.05) == o.theta_max(1 / 6)
+    xs = np.linspace(1 / 6, 1, 50)
+    th = [o.theta_max(x) for x in xs]
+    assert all(a > b for a, b in zip(th, th[1:]))
+    assert abs(o.theta_max(0.5) - 5 * math.pi / 9 * math.sqrt(1 - math.sqrt(0.4))) < 1e-15
+
+
+def check_cone_distribution():
+    """Thermalised spins are unit vectors within theta_max of the cell direction, with the
+    polar angle uniform in [0, theta_max] (its mean is theta_max / 2 and the mean spin is
+    e3 sin(theta_max)/theta_max, the azimuth averaging the transverse part away)."""
+    from scipy import stats
+    rng = np.random.default_rng(5)
+    for e3 in (np.array([0.0, 0.0, 1.0]), np.array([0.0, 0.0, -1.0]), rng.normal(size=3)):
+        e3 = e3 / np.linalg.norm(e3)
+        thm = 1.1
+        S = np.array([o.cone_sample(e3, thm, 9, s, 2) for s in range(6000)])
+        assert np.all(np.abs(np.linalg.norm(S, axis=1) - 1) < 1e-14)
+        th = np.arccos(np.clip(S @ e3, -1, 1))
+        assert th.max() <= thm + 1e-12
+        assert stats.kstest(th / thm, "uniform").pvalue > 1e-4
+        mean = S.mean(axis=0)
+        assert np.linalg.norm(mean - e3 * math.sin(thm) / thm) < 0.03
+    # theta_max = 0 returns the cell direction itself
+    e3 = np.array([0.6, 0.0, 0.8])
+    assert np.allclose(o.cone_sample(e3, 0.0, 1, 2, 3), e3, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- coupled window
+def _uniform_cells(p, v=(0.0, 0.0, 1.0)):
+    m = np.zeros((p.n_cells, 3))
+    m[:] = v
+    return m
+
+
+def check_eq6_average_brute_force():
+    """Eq. 6: after a zero-step run every window cell holds the direction of the sum of the
+    spins inside it (brute force over the cell's sites); cells outside keep their m."""
+    p = o.MsParams(9, 3, 2, 2 * A, 2, 4, J=J_SC, ku=KU, seed=4)
+    grain = np.zeros(p.n_cells, np.int32)
+    grain[5] = -1
+    O = o.MsOracle(p, grain)
+    m0 = _uniform_cells(p, (0.0, 0.6, 0.8))
+    O.set_cells(m0)
+    O.set_window(3)
+    rng = np.random.default_rng(2)
+    S = rng.normal(size=(O.nw, 3))
+    S /= np.linalg.norm(S, axis=1)[:, None]
+    nxw, nyw, nzw = p.window_dims
+    r = p.ratio
+    for k in range(nzw):
+        for j in range(nyw):
+            for i in range(nxw):
+                q = (3 + i // r) + p.ncx * (j // r + p.ncy * (k // r))
+                if grain[q] < 0:
+                    S[i + nxw * (j + nyw * k)] = 0.0
+    O.set_moments(S)
+    O.run(0)
+    m = O.cells()
+    for q in range(p.n_cells):
+        cx, cy, cz = q % p.ncx, (q // p.ncx) % p.ncy, q // (p.ncx * p.ncy)
+        if not 3 <= cx < 7:
+            want = m0[q] if grain[q] >= 0 else np.zeros(3)
+        elif grain[q] < 0:
+            want = np.zeros(3)
+        else:
+            s = np.zeros(3)
+            for dk in range(r):
+                for dj in range(r):
+                    for di in range(r):
+                        i, j, k = (cx - 3) * r + di, cy * r + dj, cz * r + dk
+                        s += S[i + nxw * (j + nyw * k)]
+            want = s / np.linalg.norm(s)
+        assert np.allclose(m[q], want, atol=1e-14), q
+
+
+def check_uniform_state_stationary_through_shifts():
+    """A uniform state along the field at T = 0 feels no torque on either side of the
+    interface, and a window moving with the spot thermalises with theta_max = 0 (m_e = 1):
+    every spin and every cell stays exactly along z through several shifts."""
+    p = o.MsParams(14, 2, 2, 2 * A, 2, 4, J=J_SC, ku=KU, dt=1e-16, seed=3, B0=0.5,
+                   direction=(0, 0, 1), fwhm=0.0, x0=6 * 2 * A, vx=2 * A / (10 * 1e-16))
+    O = o.MsOracle(p)
+    O.set_cells(_uniform_cells(p))
+    O.set_window(o.ms_target(p, 0.0))
+    w0 = O.window
+    O.run(45, follow=True)
+    assert w0 == 4 and O.window == o.ms_target(p, 45 * 1e-16) == 9
+    S = O.moments()
+    assert np.array_equal(S, np.tile([0.0, 0.0, 1.0], (O.nw, 1)))
+    assert np.array_equal(O.cells(), _uniform_cells(p))
+
+
+def check_isolated_cell_llg():
+    """One micromagnetic cell with no magnetic neighbour, uniform T, field B along z
+    (Eq. 1 without thermal field, Eq. 5 with K(T)/Ms(T) = K0 m_e^2 / Ms0, Sec. II):
+    without damping it precesses at gamma (B + (2 K0 m_e^2 / Ms0) cos theta) at constant
+    theta; with damping and no anisotropy, tan(theta/2) decays as
+    exp(-alpha gamma B t / (1 + alpha^2)) with alpha = lambda (1 - T / 3 T_C)."""
+    B0, T, dt, n = 1.0, 350.0, 2e-15, 400
+    for lam, ku in ((0.0, KU), (0.1, 0.0)):
+        p = o.MsParams(6, 1, 1, A, 1, 1, J=J_SC, ku=ku, lam=lam, dt=dt, T_amb=T, B0=B0, direction=(0, 0, 1))
+        grain = np.array([-1, -1, -1, -1, 0, -1], np.int32)
+        O = o.MsOracle(p, grain)
+        th0 = 0.4
+        m = np.zeros((6, 3))
+        m[4] = (math.sin(th0), 0.0, math.cos(th0))
+        O.set_cells(m)
+        O.set_window(0)
+        O.run(n)
+        got = O.cells()[4]
+        t = n * dt
+        me = o.me(p.T_C, T, MU_S, B0)
+        if lam == 0.0:
+            w = G * (B0 + 2 * p.K0 * me ** 2 / p.Ms0 * math.cos(th0))
+            want = np.array([math.sin(th0) * math.cos(w * t), math.sin(th0) * math.sin(w * t), math.cos(th0)])
+        else:
+            al = lam * (1 - T / (3 * p.T_C))
+            th = 2 * math.atan(math.tan(th0 / 2) * math.exp(-al * G * B0 * t / (1 + al * al)))
+            ph = G * B0 * t / (1 + al * al)
+            want = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        assert np.linalg.norm(got - want) < 1e-8, (lam, got, want)
+
+
+def check_mm_standing_spin_wave():
+    """Micromagnetic exchange at temperature (Eq. 4 with A(T)/Ms(T) = A0 m_e / Ms0, Eq. 5
+    with K(T)/Ms(T) = K0 m_e^2 / Ms0): on an open chain of N cells, the small standing wave
+    m_x + i m_y = eps cos(pi n (i + 1/2) / N) precesses without damping at
+    gamma [B + 2 K0 m_e^2 / Ms0 + (2 A0 m_e / Ms0) (2 - 2 cos(pi n / N)) / c^2], the
+    eigenvalue of the 6-point Laplacian with missing neighbours left out."""
+    N, c, T, B0, eps = 16, 1e-9, 400.0, 0.5, 1e-4
+    p = o.MsParams(N + 1, 1, 1, c, 4, 1, J=J_SC, ku=KU, lam=0.0, dt=1e-16, T_amb=T, B0=B0,
+                   direction=(0, 0, 1), A0=J_SC / (2 * A), Ms0=MU_S / A ** 3, K0=KU / A ** 3)
+    grain = np.zeros(N + 1, np.int32)
+    grain[0] = -1                       # the window's cell: no atomistic sites
+    me = o.me(p.T_C, T, MU_S, B0)
+    for n in (1, 3):
+        O = o.MsOracle(p, grain)
+        i = np.arange(N)
+        amp = eps * np.cos(np.pi * n * (i + 0.5) / N)
+        m = np.zeros((N + 1, 3))
+        m[1:, 0] = amp
+        m[1:, 2] = np.sqrt(1 - amp ** 2)
+        O.set_cells(m)
+        O.set_window(0)
+        steps = 300
+        O.run(steps)
+        got = O.cells()[1:]
+        w = G * (B0 + 2 * p.K0 * me ** 2 / p.Ms0 + 2 * p.A0 * me / p.Ms0 * (2 - 2 * math.cos(math.pi * n / N)) / c ** 2)
+        ph = np.arctan2(got[:, 1], got[:, 0])
+        k = int(np.argmax(amp))
+        want = w * steps * p.drv.dt
+        assert abs((ph[k] - want + math.pi) % (2 * math.pi) - math.pi) < 1e-4 * want, (n, ph[k], want)
+
+
+def _tilted(n, seed, deg):
+    rng = np.random.default_rng(seed)
+    th = np.deg2rad(deg) * rng.random(n)
+    ph = 2 * np.pi * rng.random(n)
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+
+
+def _coupled_vs_atomistic(dt, n_steps):
+    """Largest spin difference between the multiscale run with one site per cell and the
+    atomistic oracle on the whole lattice, from the same tilted state, at T = 0."""
+    ncx, ncy, ncz, wx, ox = 12, 5, 3, 4, 4
+    grain = np.zeros(ncx * ncy * ncz, np.int32)
+    grain.reshape(ncz, ncy, ncx)[:, :, 9] = -1      # a void column: an interface of its own
+    grain.reshape(ncz, ncy, ncx)[:, :, 10:] = 1     # and a second grain behind it
+    kw = dict(ku=KU, dt=dt, B0=0.7, direction=(0.3, 0.0, -1.0), T_amb=0.0, seed=5)
+    p = o.MsParams(ncx, ncy, ncz, A, 1, wx, J=J_SC, lam=0.1, **kw)
+    S0 = _tilted(p.n_cells, 1, 40.0)
+    S0[grain < 0] = 0.0
+    O = o.MsOracle(p, grain)
+    O.set_cells(S0)
+    O.set_window(ox)
+    win = S0.reshape(ncz, ncy, ncx, 3)[:, :, ox:ox + wx].reshape(-1, 3)
+    O.set_moments(np.ascontiguousarray(win))
+    O.run(n_steps)
+    ms = O.cells()
+    pa = o.sc_params(ncx, ncy, ncz, A, J_SC, mu_s=MU_S, alpha=0.1, **kw)
+    Oa = o.Oracle(pa, grain)
+    S = np.ascontiguousarray(S0.copy())
+    Oa.run(S, 0, n_steps)
+    return np.abs(ms - S).max()
+
+
+def check_ratio_one_window_matches_atomistic_lattice():
+    """With one site per cell (cell edge = a), Ms0 = mu_s / a^3, K0 = ku / a^3 (Appendix A)
+    and A0 = J / 2a (Eq. 9), at T = 0 (m_e = 1, alpha = lambda), the micromagnetic field
+    (2A0/Ms0) lap(m) + (2K0/Ms0) m_z z differs from the atomistic one of Eq. 2-3 only by a
+    term along m, so the coupled window and the plain atomistic lattice solve the same
+    equations.  They differ only in how they are integrated: RK4 outside, Heun inside, and
+    each region stepped with the other's interface values frozen at t_n, a splitting of
+    first order in dt.  So the difference must shrink in proportion to dt; a wrong interface
+    bond on either side leaves a difference that does not shrink."""
+    T_end = 2e-14
+    e = [_coupled_vs_atomistic(dt, int(round(T_end / dt))) for dt in (2e-16, 1e-16, 5e-17)]
+    assert e[2] < 2.5e-3, e
+    assert 1.8 < e[0] / e[1] < 2.2 and 1.8 < e[1] / e[2] < 2.2, e
+
+
+def check_full_window_equals_atomistic_oracle():
+    """A window covering the whole track with one site per cell leaves no micromagnetic
+    cell to evolve; its sites then follow the atomistic oracle exactly (same Philox stream:
+    the track site index equals the lattice site index), with thermal noise, laser spot and
+    granular decoupling on."""
+    ncx, ncy, ncz = 7, 5, 3
+    grain = np.zeros(ncx * ncy * ncz, np.int32)
+    grain.reshape(ncz, ncy, ncx)[:, 2, :] = -1
+    grain.reshape(ncz, ncy, ncx)[:, 3:, :] = 1
+    kw = dict(ku=KU, dt=1e-16, B0=0.8, direction=(0.0, 0.0, -1.0), T_amb=300.0, T_peak=800.0,
+              fwhm=1e-9, x0=0.8e-9, y0=0.5e-9, vx=1e4, seed=11)
+    p = o.MsParams(ncx, ncy, ncz, A, 1, ncx, J=J_SC, lam=0.1, **kw)
+    S0 = _tilted(p.n_cells, 4, 30.0)
+    S0[grain < 0] = 0.0
+    O = o.MsOracle(p, grain)
+    O.set_cells(S0)
+    O.set_window(0)
+    O.set_moments(S0)
+    O.run(60)
+    pa = o.sc_params(ncx, ncy, ncz, A, J_SC, mu_s=MU_S, alpha=0.1, **kw)
+    S = np.ascontiguousarray(S0.copy())
+    o.Oracle(pa, grain).run(S, 0, 60)
+    assert np.abs(O.moments() - S).max() < 1e-13
+
+
+def check_shift_moves_spins():
+    """One window move (Fig. 1): the sites shift back by one cell column, the trailing
+    column is handed to the micromagnetic side by Eq. 6 and the new leading column is
+    thermalised from its cells (at T = 0, theta_max = 0: the cell direction itself).  The
+    step before it is made negligibly short."""
+    ncx, ncy, ncz, r, wx = 10, 2, 1, 2, 4
+    p = o.MsParams(ncx, ncy, ncz, 2 * A, r, wx, J=J_SC, ku=KU, dt=1e-28, T_amb=0.0,
+                   x0=5 * 2 * A, vx=0.6 * 2 * A / 1e-28, seed=2)
+    O = o.MsOracle(p)
+    m0 = _tilted(p.n_cells, 6, 60.0)
+    O.set_cells(m0)
+    O.set_window(3)
+    S0 = _tilted(O.nw, 7, 60.0)
+    O.set_moments(S0)
+    O.run(1, follow=True)
+    assert O.window == 4
+    nxw, nyw, nzw = p.window_dims
+    S = O.moments().reshape(nzw, nyw, nxw, 3)
+    S0 = S0.reshape(nzw, nyw, nxw, 3)
+    assert np.abs(S[:, :, :nxw - r] - S0[:, :, r:]).max() < 1e-9
+    m = O.cells().reshape(ncz, ncy, ncx, 3)
+    m0 = m0.reshape(ncz, ncy, ncx, 3)
+    for cy in range(ncy):
+        lead = m0[0, cy, 7]
+        assert np.abs(S[:, cy * r:(cy + 1) * r, nxw - r:] - lead).max() < 1e-12
+        s = S0[:, cy * r:(cy + 1) * r, :r].reshape(-1, 3).sum(axis=0)
+        assert np.abs(m[0, cy, 3] - s / np.linalg.norm(s)).max() < 1e-9
+
+
+def check_window_target():
+    """The window is centred on the laser spot and stays on the track."""
+    p = o.MsParams(20, 1, 1, 1e-9, 4, 6, J=J_SC, x0=10.2e-9, vx=1.0)
+    assert o.ms_target(p, 0.0) == 7
+    assert o.ms_target(p, 5e-9) == 12
+    assert o.ms_target(p, 1.0) == 14
+    p2 = o.MsParams(20, 1, 1, 1e-9, 4, 6, J=J_SC, x0=-3e-9)
+    assert o.ms_target(p2, 0.0) == 0
+
+
+FAST_CHECKS = [
+    check_langevin_branches, check_me_limits, check_micromagnetic_damping_law,
+    check_theta_max_printed_values, check_cone_distribution, check_eq6_average_brute_force,
+    check_uniform_state_stationary_through_shifts, check_isolated_cell_llg, check_mm_standing_spin_wave,
+    check_ratio_one_window_matches_atomistic_lattice, check_full_window_equals_atomistic_oracle,
+    check_shift_moves_spins, check_window_target,
+]
