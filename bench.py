@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-ms", action="store_true", help="skip the multiscale-track line")
+    p.add_argument("--ms-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--tile", default=None, help="fused-kernel shape THREADSxSTAGED instead of autotuning")
     return p.parse_args()
@@ -287,6 +289,63 @@ def cpu_baseline_one_core(workload, seconds):
         return None
 
 
+def multiscale_line(args, dist):
+    """The full multiscale track (500 x 60 x 10 nm of 1 nm micromagnetic cells with a 60 nm
+    atomistic window of 240 x 240 x 40 sites at 0.25 nm, FP64, window following the laser):
+    coupled steps per second, as atomistic spin-steps/s of the window and cell-steps/s of the
+    track, timed with CUDA events on the library's stream; beside it the FP64 oracle's
+    coupled step on the host cores (rank 0, one process only)."""
+    import torch
+    from paper_2502_02236_gb300 import inputs as I
+    from paper_2502_02236_gb300.hamr import Multiscale
+    w = I.multiscale_track()
+    G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                   ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
+                   seed=w["seed"] ^ (dist.rank << 48))
+    G.set_grain_map(w["grain"])
+    G.set_temperature_profile(**w["T"])
+    G.set_field_sequence(**w["field"])
+    m = np.zeros((G.n_cells, 3))
+    m[:, 2] = 1.0
+    G.set_cells(m)
+    ox = int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5))
+    G.set_window(ox)
+    G.steps(3, follow=True)
+    K = max(1, args.ms_steps)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.steps(K, follow=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    G.close()
+    nw, nc = G.n_window, G.n_cells
+    line = {"workload": "multiscale_track", "dtype": "f64", "window_sites": nw, "cells": nc, "steps": K,
+            "ms_per_step": ms / K, "window_spin_steps_per_s": nw * K * dist.world / (ms / 1e3),
+            "cell_steps_per_s": nc * K * dist.world / (ms / 1e3),
+            "launches_per_step": 10, "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot"}
+    if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        import oracle as orc
+        T, F = w["T"], w["field"]
+        p = orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                         ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
+                         seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
+                         bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"])
+        O = orc.MsOracle(p, w["grain"])
+        O.set_cells(m)
+        O.set_window(ox)
+        O.run(1, follow=True)
+        t0 = time.perf_counter()
+        O.run(2, follow=True)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nw * 2 / el, "unit": "window spin-steps/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": "2 coupled steps of the full track in %.1f s" % el}
+    return line
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -388,6 +447,9 @@ def main():
         out["e2e"] = {"value": n_sites * K * dist.world / el, "unit": "spin-steps/s",
                       "h2d_bytes_per_step": hb / K, "d2h_bytes_per_step": d2h / K,
                       "note": "per call: H2D of all spins, K steps, D2H of M(t) and all spins; bytes / K"}
+
+    if not args.no_ms and args.workload == "ensemble256":
+        out["multiscale"] = multiscale_line(args, dist)
 
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
         v, reps, n, steps, el = cpu_baseline(w, args.cpu_seconds)

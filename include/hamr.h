@@ -269,6 +269,92 @@ const char *hamr_last_error(hamr_t h);
 /* Free all device and host memory of the handle.  NULL is allowed. */
 void hamr_destroy(hamr_t h);
 
+
+/* ------------------------------------------------------------------------------------
+ * Multiscale write window (Sec. II and Fig. 1 of the paper).
+ *
+ * A micromagnetic track of ncx x ncy x ncz cubic cells (edge `cell`) holds an atomistic
+ * simple-cubic window of spacing a = cell / ratio: the window is wx cell columns long,
+ * starts at cell column x0 and spans every cell in y and z, so each of its cells holds
+ * ratio^3 sites.  A cell's grain id (-1 = non-magnetic) is shared by its sites.  FP64.
+ * One coupled step n -> n+1, drivers frozen at t_n:
+ *   1. every window cell takes the direction of the sum of its spins (Eq. 6);
+ *   2. the window takes one sLLG Heun step as in hamr_sllg_heun_steps (Eq. 1-3, damping
+ *      lambda, thermal normals keyed by the seed with the site's index on the whole track,
+ *      X + (ncx ratio)(j + (ncy ratio) k), X = x0 ratio + i); a bond across the window's
+ *      x faces sees the direction m of the micromagnetic cell holding the neighbour
+ *      position (Eq. 2 with the cell's m).  Bonds join equal grain ids only;
+ *   3. the cells outside the window take one classical RK4 step of the micromagnetic LLG
+ *      (Eq. 1 without thermal field) in the field
+ *        B = (2 A(T)/Ms(T)) lap(m) + (2 K(T)/Ms(T)) (m.z) z + B_app          (Eq. 4, 5)
+ *      with the 6-point finite-difference Laplacian over same-grain magnetic cells (a
+ *      missing neighbour adds nothing; window cells enter with their Eq. 6 directions),
+ *      Ms(T) = Ms0 m_e, A(T) = A0 m_e^2, K(T) = K0 m_e^3, damping
+ *      lambda (1 - T / 3 T_C) with T capped at T_C, and m_e(T) the root in [0, 1] of
+ *      m = L(3 T_C m / T + mu_s |B_app| / kB T), L(x) = coth x - 1/x (Sec. II); T is the
+ *      laser temperature at the cell centre; m is renormalised after the step.
+ * Moving the window one column forward (hamr_ms_steps with follow): the trailing column
+ * is handed to the micromagnetic side by Eq. 6, the sites shift back by one cell column
+ * and the new leading column is thermalised: each site gets a spin whose polar angle from
+ * the cell's m is uniform in [0, theta_max], theta_max = (5 pi/9) sqrt(1 - sqrt(1 +
+ * 6 (m_e - 1)/5)) with the root's argument held in [0, 1] (Sec. II, M/Ms0 = m_e of the
+ * cell), and whose azimuth is uniform; u0, u1 are the first two words of Philox4x32-10
+ * with key = seed and counter = (site low, site high, event low, event high | 2^31),
+ * event = the number of thermalisations so far (window placements and moves).
+ * Conventions are those of the rest of this header; cell and site arrays at the boundary
+ * are FP64 AoS, x fastest.  Sites of the window: i + nxw (j + nyw k) with nxw = wx ratio,
+ * nyw = ncy ratio.
+ * ------------------------------------------------------------------------------------ */
+typedef struct hamr_ms_ctx *hamr_ms_t;
+
+typedef struct {
+    int32_t ncx, ncy, ncz;   /* micromagnetic cells along x (the track), y, z */
+    double cell;             /* cell edge [m] */
+    int32_t ratio;           /* atomistic sites per cell edge, >= 1 */
+    int32_t wx;              /* window length in cells, 1 <= wx <= ncx */
+    double J, mu_s, ku;      /* atomistic exchange [J], moment [J/T], anisotropy per atom [J] */
+    double Ms0, A0, K0;      /* micromagnetic Ms [A/m], A [J/m], K [J/m^3] at 0 K */
+    double lambda;           /* atomistic damping (the paper's lambda) */
+    double T_C;              /* Curie temperature of the m_e(T) law [K] */
+    double gamma, dt;        /* [rad/(s T)], [s] */
+    uint64_t seed;           /* Philox key */
+    int32_t device;
+    void *stream;            /* cudaStream_t, or NULL for a library-owned stream */
+} hamr_ms_desc;
+
+/* Allocates the track and the window (errors: ARG, OOM, CUDA; message in
+ * hamr_ms_last_error(NULL)).  Cells start at m = 0, every cell in grain 0. */
+int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d);
+/* Grain id per cell (ncx ncy ncz int32, -1 = non-magnetic; copied).  ARG on ids < -1. */
+int hamr_ms_set_grain_map(hamr_ms_t h, const int32_t *cell_grain);
+/* Laser spot and write field, as hamr_set_temperature_profile / hamr_set_field_sequence
+ * (Sec. III, Fig. 2), shared by both regions. */
+int hamr_ms_set_temperature_profile(hamr_ms_t h, double T_amb, double T_peak, double fwhm, double x0, double y0,
+                                    double vx, double vy);
+int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], const uint8_t *bits, int32_t n_bits,
+                               double bit_len, double ramp_len, double head_x0, double head_v);
+/* Micromagnetic directions m (3 ncx ncy ncz doubles, AoS; copied; non-magnetic cells are
+ * set to 0).  ARG on non-finite values. */
+int hamr_ms_set_cells(hamr_ms_t h, const double *m);
+/* Places the window at cell column x0_cells and thermalises all of it from the cells (one
+ * thermalisation event).  ARG if the window leaves the track, STATE before set_cells. */
+int hamr_ms_set_window(hamr_ms_t h, int32_t x0_cells);
+/* Overwrites the window's spins (3 nxw nyw nzw doubles, AoS; copied).  STATE before the
+ * window is placed. */
+int hamr_ms_set_moments(hamr_ms_t h, const double *S);
+/* n_steps coupled steps; follow != 0 moves the window forward after each step until it is
+ * centred on the laser spot, x0 = floor(x_spot / cell - wx/2 + 1/2) kept on the track.
+ * Window cells then hold the Eq. 6 directions of the current spins.  ARG on n_steps < 0,
+ * STATE before the window is placed. */
+int hamr_ms_steps(hamr_ms_t h, int64_t n_steps, int32_t follow);
+/* Reads m (3 ncx ncy ncz doubles) or the window spins (3 nxw nyw nzw doubles). */
+int hamr_ms_read_cells(hamr_ms_t h, double *m_out);
+int hamr_ms_read_moments(hamr_ms_t h, double *S_out);
+/* Window column (-1 before placement) and completed steps; either pointer may be NULL. */
+int hamr_ms_get_window(hamr_ms_t h, int32_t *x0_cells, int64_t *step);
+const char *hamr_ms_last_error(hamr_ms_t h);
+void hamr_ms_destroy(hamr_ms_t h);
+
 #ifdef __cplusplus
 }
 #endif

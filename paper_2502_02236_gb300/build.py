@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhamr.so")
-SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused_sc.cu", "kernels_fused_l10.cu", "kernels_misc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_plain.cu", "kernels_fused_sc.cu", "kernels_fused_l10.cu", "kernels_misc.cu", "noalloc.cu",
+           "multiscale.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -49,6 +50,10 @@ def build(force=False, verbose=False, extra=()):
             # the fused kernels write every multiply-add out (identical rounding in every
             # instantiation, see kernels_fused.cuh)
             fmad = ["-fmad=false"] if src.startswith("kernels_fused") else []
+            # the multiscale driver decides on the host when the window moves; its host
+            # arithmetic rounds every multiply and add on its own on every platform
+            if src == "multiscale.cu":
+                fmad = ["-Xcompiler", "-ffp-contract=off"]
             jobs.append([nvcc(), *flags(), *fmad, *extra, "-c", s, "-o", o])
 
     def run(cmd):

@@ -27,6 +27,10 @@ EXPORTS = [
     "hamr_set_step", "hamr_check_finite", "hamr_save_state", "hamr_load_state", "hamr_set_tile",
     "hamr_get_tile", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
     "hamr_sllg_heun_step_noalloc", "hamr_inject_wait_timeout",
+    "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
+    "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
+    "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window",
+    "hamr_ms_last_error", "hamr_ms_destroy",
 ]
 NOALLOC_MAX_SITES = 131072
 
@@ -60,6 +64,18 @@ class NoallocParams(ctypes.Structure):
         ("T_amb", ctypes.c_double), ("T_peak", ctypes.c_double), ("fwhm", ctypes.c_double),
         ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("vx", ctypes.c_double),
         ("vy", ctypes.c_double), ("B_app", ctypes.c_double * 3),
+    ]
+
+
+class MsDesc(ctypes.Structure):
+    _fields_ = [
+        ("ncx", ctypes.c_int32), ("ncy", ctypes.c_int32), ("ncz", ctypes.c_int32),
+        ("cell", ctypes.c_double), ("ratio", ctypes.c_int32), ("wx", ctypes.c_int32),
+        ("J", ctypes.c_double), ("mu_s", ctypes.c_double), ("ku", ctypes.c_double),
+        ("Ms0", ctypes.c_double), ("A0", ctypes.c_double), ("K0", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("T_C", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -103,6 +119,17 @@ def lib():
             "hamr_query": [vp, i32, vp],
             "hamr_sllg_heun_step_noalloc": [vp, vp, vp, vp, i64, vp],
             "hamr_inject_wait_timeout": [vp, i32],
+            "hamr_ms_create": [vp, vp],
+            "hamr_ms_set_grain_map": [vp, vp],
+            "hamr_ms_set_temperature_profile": [vp, d, d, d, d, d, d, d],
+            "hamr_ms_set_field_sequence": [vp, d, vp, vp, i32, d, d, d, d],
+            "hamr_ms_set_cells": [vp, vp],
+            "hamr_ms_set_window": [vp, i32],
+            "hamr_ms_set_moments": [vp, vp],
+            "hamr_ms_steps": [vp, i64, i32],
+            "hamr_ms_read_cells": [vp, vp],
+            "hamr_ms_read_moments": [vp, vp],
+            "hamr_ms_get_window": [vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -112,6 +139,10 @@ def lib():
         L.hamr_last_error.restype = ctypes.c_char_p
         L.hamr_destroy.argtypes = [vp]
         L.hamr_destroy.restype = None
+        L.hamr_ms_last_error.argtypes = [vp]
+        L.hamr_ms_last_error.restype = ctypes.c_char_p
+        L.hamr_ms_destroy.argtypes = [vp]
+        L.hamr_ms_destroy.restype = None
         _lib = L
     return _lib
 
@@ -348,3 +379,100 @@ def sllg_heun_step_noalloc(dims, S_in, S_out, *, grain=None, step=0, periodic=(F
                                            ctypes.c_void_p(S_out.data_ptr()), g, int(step), stream)
     if rc != OK:
         raise HamrError(rc, lib().hamr_last_error(None).decode())
+
+
+class Multiscale:
+    """One hamr_ms_t handle: the multiscale write window (an atomistic simple-cubic window
+    in a micromagnetic track, FP64).  Cell arrays are (ncx*ncy*ncz, 3), window spins
+    (nxw*nyw*nzw, 3), x fastest."""
+
+    def __init__(self, ncx, ncy, ncz, cell, ratio, wx, *, J, mu_s, ku, Ms0, A0, K0, lam, T_C,
+                 dt=1e-16, gamma=GAMMA, seed=1, device=None, stream="torch"):
+        L = lib()
+        d = MsDesc()
+        d.ncx, d.ncy, d.ncz, d.cell, d.ratio, d.wx = ncx, ncy, ncz, cell, ratio, wx
+        d.J, d.mu_s, d.ku, d.Ms0, d.A0, d.K0 = J, mu_s, ku, Ms0, A0, K0
+        d.lambda_, d.T_C, d.gamma, d.dt, d.seed = lam, T_C, gamma, dt, int(seed)
+        tdev, tstream = _torch_current()
+        d.device = tdev if device is None else device
+        d.stream = tstream if stream == "torch" else stream
+        self.n_cells = ncx * ncy * ncz
+        self.window_dims = (wx * ratio, ncy * ratio, ncz * ratio)
+        self.n_window = int(np.prod(self.window_dims))
+        h = ctypes.c_void_p()
+        rc = L.hamr_ms_create(ctypes.byref(h), ctypes.byref(d))
+        if rc != OK:
+            raise HamrError(rc, L.hamr_ms_last_error(None).decode())
+        self._h = h
+
+    def _ck(self, rc):
+        if rc != OK:
+            raise HamrError(rc, lib().hamr_ms_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hamr_ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_grain_map(self, cell_grain):
+        g = np.ascontiguousarray(np.asarray(cell_grain, dtype=np.int32).reshape(-1))
+        if g.size != self.n_cells:
+            raise ValueError("one grain id per cell")
+        self._ck(lib().hamr_ms_set_grain_map(self._h, _p(g)))
+
+    def set_temperature_profile(self, T_amb, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0):
+        self._ck(lib().hamr_ms_set_temperature_profile(self._h, T_amb, T_peak, fwhm, x0, y0, vx, vy))
+
+    def set_field_sequence(self, B0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0, ramp_len=0.0,
+                           head_x0=0.0, head_v=0.0):
+        dr = np.ascontiguousarray(np.asarray(direction, dtype=np.float64))
+        b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
+        self._ck(lib().hamr_ms_set_field_sequence(self._h, B0, _p(dr), _p(b) if b.size else None, b.size,
+                                                  bit_len, ramp_len, head_x0, head_v))
+
+    def set_cells(self, m):
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(-1))
+        if m.size != 3 * self.n_cells:
+            raise ValueError("three components per cell")
+        self._ck(lib().hamr_ms_set_cells(self._h, _p(m)))
+
+    def set_window(self, x0_cells):
+        self._ck(lib().hamr_ms_set_window(self._h, int(x0_cells)))
+
+    def set_moments(self, S):
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(-1))
+        if S.size != 3 * self.n_window:
+            raise ValueError("three components per window site")
+        self._ck(lib().hamr_ms_set_moments(self._h, _p(S)))
+
+    def steps(self, n_steps, follow=False):
+        self._ck(lib().hamr_ms_steps(self._h, int(n_steps), int(bool(follow))))
+
+    def read_cells(self):
+        m = np.zeros((self.n_cells, 3))
+        self._ck(lib().hamr_ms_read_cells(self._h, _p(m)))
+        return m
+
+    def read_moments(self):
+        S = np.zeros((self.n_window, 3))
+        self._ck(lib().hamr_ms_read_moments(self._h, _p(S)))
+        return S
+
+    def window(self):
+        ox = ctypes.c_int32()
+        st = ctypes.c_int64()
+        self._ck(lib().hamr_ms_get_window(self._h, ctypes.byref(ox), ctypes.byref(st)))
+        return ox.value, st.value

@@ -16,6 +16,7 @@ import math
 import numpy as np
 
 MU_B = 9.2740100783e-24          # Bohr magneton [J/T]
+KB = 1.380649e-23               # Boltzmann constant [J/K]
 GAMMA = 1.76085963023e11         # electron gyromagnetic ratio [rad/(s T)]
 
 #: The bit pattern written in the paper's track simulations (Sec. III, Fig. 3).
@@ -200,3 +201,25 @@ def workload(name, **over):
     w.update(over)
     w["name"] = name
     return w
+
+
+def multiscale_track(ncx=500, ncy=60, ncz=10, cell=1e-9, ratio=4, wx=60, grain_d=8e-9, boundary=1e-9, seed=14,
+                     T_peak=800.0, v=20.0, x_spot=None):
+    """The multiscale track: ncx x ncy x ncz micromagnetic cells of edge `cell` (by default
+    500 x 60 x 10 nm at 1 nm) with an atomistic simple-cubic window of spacing cell / ratio
+    (0.25 nm) wx cells long (60 nm: 240 x 240 x 40 sites) over the hot spot; Voronoi grains
+    of mean diameter grain_d at cell resolution with `boundary`-wide non-magnetic borders;
+    50 nm FWHM laser, T_peak over 300 K, moving at v; +/-0.8 T write field of 20 nm bits with
+    the paper's pattern.  The micromagnetic constants are the atomistic ones per unit volume
+    (Ms0 = mu_s / a^3, K0 = ku / a^3) and A0 = J / 2a; T_C = 1.443 J / kB.  Returns a dict
+    of these inputs; cells start along +z."""
+    a = cell / ratio
+    g2 = voronoi_grains(ncx, ncy, cell, cell, grain_d, boundary, seed)
+    grain = columnar(g2, ncz)
+    xs = (wx / 2.0 + 1.0) * cell if x_spot is None else x_spot
+    return dict(ncx=ncx, ncy=ncy, ncz=ncz, cell=cell, ratio=ratio, wx=wx, grain=grain,
+                J=J_SC, mu_s=MU_S, ku=KU_SC, Ms0=MU_S / a ** 3, A0=J_SC / (2 * a), K0=KU_SC / a ** 3,
+                lam=0.1, T_C=1.443 * J_SC / KB, dt=1e-16, seed=seed,
+                T=dict(T_amb=300.0, T_peak=T_peak, fwhm=50e-9, x0=xs, y0=ncy * cell / 2, vx=v, vy=0.0),
+                field=dict(B0=0.8, direction=(0.0, 0.0, 1.0), bits=bits_of(PAPER_BIT_PATTERN), bit_len=20e-9,
+                           ramp_len=2e-9, head_x0=xs, head_v=v))
