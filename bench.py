@@ -291,41 +291,48 @@ def cpu_baseline_one_core(workload, seconds):
 
 def multiscale_line(args, dist):
     """The full multiscale track (500 x 60 x 10 nm of 1 nm micromagnetic cells with a 60 nm
-    atomistic window of 240 x 240 x 40 sites at 0.25 nm, FP64, window following the laser):
-    coupled steps per second, as atomistic spin-steps/s of the window and cell-steps/s of the
-    track, timed with CUDA events on the library's stream; beside it the FP64 oracle's
-    coupled step on the host cores (rank 0, one process only)."""
+    atomistic window of 240 x 240 x 40 sites at 0.25 nm, window following the laser), FP32
+    with the FP64 rate beside it: coupled steps per second, as atomistic spin-steps/s of the
+    window and cell-steps/s of the track, timed with CUDA events on the library's stream;
+    beside them the FP64 oracle's coupled step on the host cores (rank 0, one process only)."""
     import torch
     from paper_2502_02236_gb300 import inputs as I
     from paper_2502_02236_gb300.hamr import Multiscale
     w = I.multiscale_track()
-    G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
-                   ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
-                   seed=w["seed"] ^ (dist.rank << 48))
-    G.set_grain_map(w["grain"])
-    G.set_temperature_profile(**w["T"])
-    G.set_field_sequence(**w["field"])
-    m = np.zeros((G.n_cells, 3))
+    m = np.zeros((w["ncx"] * w["ncy"] * w["ncz"], 3))
     m[:, 2] = 1.0
-    G.set_cells(m)
     ox = int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5))
-    G.set_window(ox)
-    G.steps(3, follow=True)
+
+    def rate(precision, K):
+        G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                       ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
+                       seed=w["seed"] ^ (dist.rank << 48), precision=precision)
+        G.set_grain_map(w["grain"])
+        G.set_temperature_profile(**w["T"])
+        G.set_field_sequence(**w["field"])
+        G.set_cells(m)
+        G.set_window(ox)
+        G.steps(3, follow=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.steps(K, follow=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = dist.max(e0.elapsed_time(e1))
+        G.close()
+        return ms / K, G.n_window, G.n_cells
+
     K = max(1, args.ms_steps)
-    dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    G.steps(K, follow=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = dist.max(e0.elapsed_time(e1))
-    G.close()
-    nw, nc = G.n_window, G.n_cells
-    line = {"workload": "multiscale_track", "dtype": "f64", "window_sites": nw, "cells": nc, "steps": K,
-            "ms_per_step": ms / K, "window_spin_steps_per_s": nw * K * dist.world / (ms / 1e3),
-            "cell_steps_per_s": nc * K * dist.world / (ms / 1e3),
+    t32, nw, nc = rate("fp32", 5 * K)
+    t64, _, _ = rate("fp64", K)
+    line = {"workload": "multiscale_track", "dtype": "f32", "window_sites": nw, "cells": nc, "steps": 5 * K,
+            "ms_per_step": t32, "window_spin_steps_per_s": nw * dist.world / (t32 / 1e3),
+            "cell_steps_per_s": nc * dist.world / (t32 / 1e3),
+            "fp64": {"ms_per_step": t64, "window_spin_steps_per_s": nw * dist.world / (t64 / 1e3), "steps": K},
+            "speedup_fp32_over_fp64": t64 / t32,
             "launches_per_step": 10, "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot"}
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
         import oracle as orc

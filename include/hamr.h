@@ -318,6 +318,8 @@ typedef struct {
     double T_C;              /* Curie temperature of the m_e(T) law [K] */
     double gamma, dt;        /* [rad/(s T)], [s] */
     uint64_t seed;           /* Philox key */
+    int32_t precision;       /* HAMR_FP64: everything in FP64.  HAMR_FP32: spins, cells and
+                                field arithmetic in FP32 (m_e(T) is solved in FP64) */
     int32_t device;
     void *stream;            /* cudaStream_t, or NULL for a library-owned stream */
 } hamr_ms_desc;

@@ -44,13 +44,35 @@ struct MsDev {
     unsigned key0, key1;       // Philox key = seed (low, high)
 };
 
-__device__ __forceinline__ double3 rhs(double gamma, double alpha, double sx, double sy, double sz, double bx,
-                                       double by, double bz) {
-    // -gamma/(1+alpha^2) [S x B + alpha S x (S x B)]
-    const double cx = sy * bz - sz * by, cy = sz * bx - sx * bz, cz = sx * by - sy * bx;
-    const double dx = sy * cz - sz * cy, dy = sz * cx - sx * cz, dz = sx * cy - sy * cx;
-    const double pref = -gamma / (1.0 + alpha * alpha);
-    return make_double3(pref * (cx + alpha * dx), pref * (cy + alpha * dy), pref * (cz + alpha * dz));
+template <typename Real>
+struct V3 {
+    Real x, y, z;
+};
+
+// -gamma/(1+alpha^2) [S x B + alpha S x (S x B)]
+template <typename Real>
+__device__ __forceinline__ V3<Real> rhs(Real gamma, Real alpha, Real sx, Real sy, Real sz, Real bx, Real by, Real bz) {
+    const Real cx = sy * bz - sz * by, cy = sz * bx - sx * bz, cz = sx * by - sy * bx;
+    const Real dx = sy * cz - sz * cy, dy = sz * cx - sx * cz, dz = sx * cy - sy * cx;
+    const Real pref = -gamma / (Real(1) + alpha * alpha);
+    return {pref * (cx + alpha * dx), pref * (cy + alpha * dy), pref * (cz + alpha * dz)};
+}
+
+// the laser temperature and the write field in the arithmetic of the state (FP64 or FP32
+// driver copies)
+__device__ __forceinline__ double temp_at(const ReplicaDev &D, double x, double y, double t) {
+    return temperature(D, x, y, t);
+}
+__device__ __forceinline__ float temp_at(const ReplicaDev &D, float x, float y, float t) {
+    return temperature_f(D, x, y, t);
+}
+__device__ __forceinline__ V3<double> applied_field(const ReplicaDev &D, const uint8_t *bits, double t) {
+    const double s = D.B0 * field_polarity(D, bits, t);
+    return {s * D.dir[0], s * D.dir[1], s * D.dir[2]};
+}
+__device__ __forceinline__ V3<float> applied_field(const ReplicaDev &D, const uint8_t *bits, float t) {
+    const float s = D.fB0 * field_polarity_f(D, bits, t);
+    return {s * D.fdir[0], s * D.fdir[1], s * D.fdir[2]};
 }
 
 __device__ __forceinline__ double langevin(double x) {
@@ -65,28 +87,29 @@ __device__ __forceinline__ double langevin_d(double x) {
 }
 
 // m_e(T): the largest root in [0, 1] of m = L(3 T_C m / T + mu_s B / (kB T)).  Newton steps
-// from m = 1 kept inside a bracket [lo, hi] with L(.) - m >= 0 at lo and < 0 at hi; a step
-// that leaves the bracket is replaced by bisection.
-__device__ double me_root(double T_C, double T, double mu_s, double B) {
+// from m0 (the cell's value at the previous step; 1 when there is none) kept inside a bracket
+// [lo, hi] with L(.) - m >= 0 at lo and < 0 at hi; a step that leaves the bracket is
+// replaced by bisection.  A Newton step below 1e-13 (1 + m) is taken as converged (the
+// iteration is quadratic there; the bound is absolute for small m, where coth x - 1/x loses
+// digits to cancellation and the residual is only known to about 1e-14), before the bracket
+// test, which a converged step can fail by rounding.
+__device__ double me_root(double T_C, double T, double mu_s, double B, double m0) {
     if (!(T > 0.0)) return 1.0;
     const double a = 3.0 * T_C / T, b = mu_s * B / (KB * T);
-    double lo = 0.0, hi = 1.0, m = 1.0;
-    for (int it = 0; it < 200; ++it) {
+    double lo = 0.0, hi = 1.0, m = (m0 > 0.0 && m0 <= 1.0) ? m0 : 1.0;
+    for (int it = 0; it < 300; ++it) {
         const double g = langevin(a * m + b) - m;
         if (g >= 0.0)
             lo = m;
         else
             hi = m;
         const double gp = a * langevin_d(a * m + b) - 1.0;
-        double mn = m - g / gp;
-        if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
-        if (fabs(mn - m) <= 2e-16 * m || hi - lo <= 2e-16) {
-            m = mn;
-            break;
-        }
-        m = mn;
+        const double mn = m - g / gp;
+        if (fabs(mn - m) <= 1e-13 * (1.0 + m)) return mn;
+        m = (mn > lo && mn < hi) ? mn : 0.5 * (lo + hi);
+        if (hi - lo <= 1e-16 * hi) return lo;
     }
-    return m;
+    return lo;
 }
 
 __device__ __forceinline__ double theta_max(double mr) {
@@ -95,23 +118,34 @@ __device__ __forceinline__ double theta_max(double mr) {
     return (5.0 * M_PI / 9.0) * sqrt(1.0 - sqrt(x));
 }
 
-__device__ __forceinline__ double3 applied_field(const ReplicaDev &D, const uint8_t *bits, double t) {
-    const double s = D.B0 * field_polarity(D, bits, t);
-    return make_double3(s * D.dir[0], s * D.dir[1], s * D.dir[2]);
+__device__ __forceinline__ int cell_at(const MsDev &P, int cx, int cy, int cz) {
+    return cx + P.ncx * (cy + P.ncy * cz);
 }
 
-__device__ __forceinline__ long long cell_at(const MsDev &P, long long cx, long long cy, long long cz) {
-    return cx + (long long)P.ncx * (cy + (long long)P.ncy * cz);
+// v / ratio for v >= 0, with the ratio a compile-time constant when RT != 0 (1, 2 and 4 are
+// instantiated; other ratios use the runtime value)
+template <int RT>
+__device__ __forceinline__ int per_cell(const MsDev &P, int v) {
+    return RT ? (int)((unsigned)v / (unsigned)RT) : v / P.r;
+}
+
+// 3-D launch over (x, y, z) with blocks of 32 x 4: the thread's coordinates
+__device__ __forceinline__ bool coords(int nx, int ny, int &x, int &y, int &z) {
+    x = blockIdx.x * 32 + threadIdx.x;
+    y = blockIdx.y * 4 + threadIdx.y;
+    z = blockIdx.z;
+    return x < nx && y < ny;
 }
 
 // Eq. 6 for the cells of columns [cx0, cx0 + ncol): direction of the sum of their sites.
-__global__ void k_ms_average(double *m, const double *S, const int *grain, MsDev P, int ox, int cx0, int ncol) {
+template <typename Real>
+__global__ void k_ms_average(Real *m, const Real *S, const int *grain, MsDev P, int ox, int cx0, int ncol) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n = (long long)ncol * P.ncy * P.ncz;
     if (idx >= n) return;
     const int cx = cx0 + (int)(idx % ncol), cy = (int)((idx / ncol) % P.ncy), cz = (int)(idx / ((long long)ncol * P.ncy));
-    const long long q = cell_at(P, cx, cy, cz);
-    double sx = 0.0, sy = 0.0, sz = 0.0;
+    const int q = cell_at(P, cx, cy, cz);
+    Real sx = 0, sy = 0, sz = 0;
     if (grain[q] >= 0)
         for (int dk = 0; dk < P.r; ++dk)
             for (int dj = 0; dj < P.r; ++dj)
@@ -123,197 +157,215 @@ __global__ void k_ms_average(double *m, const double *S, const int *grain, MsDev
                     sy += S[P.nw + s];
                     sz += S[2 * P.nw + s];
                 }
-    const double nn = sqrt(sx * sx + sy * sy + sz * sz);
-    m[q] = nn > 0.0 ? sx / nn : 0.0;
-    m[P.nc + q] = nn > 0.0 ? sy / nn : 0.0;
-    m[2 * P.nc + q] = nn > 0.0 ? sz / nn : 0.0;
+    const Real nn = sqrt(sx * sx + sy * sy + sz * sz);
+    m[q] = nn > Real(0) ? sx / nn : Real(0);
+    m[P.nc + q] = nn > Real(0) ? sy / nn : Real(0);
+    m[2 * P.nc + q] = nn > Real(0) ? sz / nn : Real(0);
 }
 
 // Exchange sum sum_j J v_j of window site (i, j, k) of grain g over its same-grain bonds: the
 // window spins V inside, the cells m across the window's x faces.
-__device__ __forceinline__ double3 exchange(const MsDev &P, const double *V, const double *m, const int *grain,
-                                            int ox, int i, int j, int k, int g) {
-    double ex = 0.0, ey = 0.0, ez = 0.0;
+template <typename Real, int RT>
+__device__ __forceinline__ V3<Real> exchange(const MsDev &P, const Real *V, const Real *m, const int *grain, int ox,
+                                             int i, int j, int k, int g) {
+    const Real J = (Real)P.J;
+    Real ex = 0, ey = 0, ez = 0;
     const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
         const int ii = i + off[b][0], jj = j + off[b][1], kk = k + off[b][2];
         if (jj < 0 || jj >= P.nyw || kk < 0 || kk >= P.nzw) continue;
-        double vx, vy, vz;
+        Real vx, vy, vz;
         if (ii >= 0 && ii < P.nxw) {
-            if (grain[cell_at(P, ox + ii / P.r, jj / P.r, kk / P.r)] != g) continue;
-            const long long s = ii + P.nxw * (jj + (long long)P.nyw * kk);
+            if (grain[cell_at(P, ox + per_cell<RT>(P, ii), per_cell<RT>(P, jj), per_cell<RT>(P, kk))] != g) continue;
+            const long long s = ii + (long long)P.nxw * (jj + (long long)P.nyw * kk);
             vx = V[s];
             vy = V[P.nw + s];
             vz = V[2 * P.nw + s];
         } else {
-            const long long cx = ox + (ii < 0 ? -1 : P.wx);
+            const int cx = ox + (ii < 0 ? -1 : P.wx);
             if (cx < 0 || cx >= P.ncx) continue;
-            const long long q = cell_at(P, cx, jj / P.r, kk / P.r);
+            const int q = cell_at(P, cx, per_cell<RT>(P, jj), per_cell<RT>(P, kk));
             if (grain[q] != g) continue;
             vx = m[q];
             vy = m[P.nc + q];
             vz = m[2 * P.nc + q];
         }
-        ex += P.J * vx;
-        ey += P.J * vy;
-        ez += P.J * vz;
+        ex += J * vx;
+        ey += J * vy;
+        ez += J * vz;
     }
-    return make_double3(ex, ey, ez);
+    return {ex, ey, ez};
 }
 
-__global__ void k_ms_predict(const double *S, double *Sp, double *F1, double *BTH, const double *m, const int *grain,
-                             MsDev P, ReplicaDev D, const uint8_t *bits, int ox, long long step) {
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= P.nw) return;
-    const int i = (int)(s % P.nxw), j = (int)((s / P.nxw) % P.nyw), k = (int)(s / ((long long)P.nxw * P.nyw));
-    const int g = grain[cell_at(P, ox + i / P.r, j / P.r, k / P.r)];
+template <typename Real, int RT>
+__global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const Real *m, const int *grain, MsDev P,
+                             ReplicaDev D, const uint8_t *bits, int ox, long long step) {
+    int i, j, k;
+    if (!coords(P.nxw, P.nyw, i, j, k)) return;
+    const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
+    const int g = grain[cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k))];
     if (g < 0) {
-        Sp[s] = Sp[P.nw + s] = Sp[2 * P.nw + s] = 0.0;
+        Sp[s] = Sp[P.nw + s] = Sp[2 * P.nw + s] = Real(0);
         return;
     }
-    const double t = (double)step * P.dt;
-    const double T = temperature(D, ((double)ox * P.r + i + 0.5) * P.a, (j + 0.5) * P.a, t);
-    const double sig = P.sig0 * sqrt(T);
+    const Real t = (Real)step * (Real)P.dt, a = (Real)P.a, mu = (Real)P.mu_s;
+    const Real T = temp_at(D, ((Real)ox * P.r + i + Real(0.5)) * a, (j + Real(0.5)) * a, t);
+    const Real sig = (Real)P.sig0 * sqrt(T);
     const unsigned long long X = (unsigned long long)ox * P.r + i, NX = (unsigned long long)P.ncx * P.r;
     const unsigned long long site = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * k);
-    double n0, n1, n2;
+    Real n0, n1, n2;
     normals3(philox_site(P.key0, P.key1, site, (unsigned long long)step), n0, n1, n2);
-    const double bthx = sig * n0, bthy = sig * n1, bthz = sig * n2;
+    const Real bthx = sig * n0, bthy = sig * n1, bthz = sig * n2;
     BTH[s] = bthx;
     BTH[P.nw + s] = bthy;
     BTH[2 * P.nw + s] = bthz;
-    const double3 ba = applied_field(D, bits, t);
-    const double3 ex = exchange(P, S, m, grain, ox, i, j, k, g);
-    const double sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
-    const double3 f = rhs(P.gamma, P.lambda, sx, sy, sz, ex.x / P.mu_s + ba.x + bthx, ex.y / P.mu_s + ba.y + bthy,
-                          ex.z / P.mu_s + 2.0 * P.ku / P.mu_s * sz + ba.z + bthz);
+    const V3<Real> ba = applied_field(D, bits, t);
+    const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g);
+    const Real sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
+    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, ex.x / mu + ba.x + bthx,
+                                 ex.y / mu + ba.y + bthy, ex.z / mu + Real(2) * (Real)P.ku / mu * sz + ba.z + bthz);
     F1[s] = f.x;
     F1[P.nw + s] = f.y;
     F1[2 * P.nw + s] = f.z;
-    const double vx = sx + P.dt * f.x, vy = sy + P.dt * f.y, vz = sz + P.dt * f.z;
-    const double nv = sqrt(vx * vx + vy * vy + vz * vz);
+    const Real dt = (Real)P.dt;
+    const Real vx = sx + dt * f.x, vy = sy + dt * f.y, vz = sz + dt * f.z;
+    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
     Sp[s] = vx / nv;
     Sp[P.nw + s] = vy / nv;
     Sp[2 * P.nw + s] = vz / nv;
 }
 
-__global__ void k_ms_correct(double *S, const double *Sp, const double *F1, const double *BTH, const double *m,
-                             const int *grain, MsDev P, ReplicaDev D, const uint8_t *bits, int ox, long long step) {
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= P.nw) return;
-    const int i = (int)(s % P.nxw), j = (int)((s / P.nxw) % P.nyw), k = (int)(s / ((long long)P.nxw * P.nyw));
-    const int g = grain[cell_at(P, ox + i / P.r, j / P.r, k / P.r)];
+template <typename Real, int RT>
+__global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real *BTH, const Real *m, const int *grain,
+                             MsDev P, ReplicaDev D, const uint8_t *bits, int ox, long long step) {
+    int i, j, k;
+    if (!coords(P.nxw, P.nyw, i, j, k)) return;
+    const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
+    const int g = grain[cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k))];
     if (g < 0) return;
-    const double t = (double)step * P.dt;
-    const double3 ba = applied_field(D, bits, t);
-    const double3 ex = exchange(P, Sp, m, grain, ox, i, j, k, g);
-    const double px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
-    const double3 f = rhs(P.gamma, P.lambda, px, py, pz, ex.x / P.mu_s + ba.x + BTH[s],
-                          ex.y / P.mu_s + ba.y + BTH[P.nw + s],
-                          ex.z / P.mu_s + 2.0 * P.ku / P.mu_s * pz + ba.z + BTH[2 * P.nw + s]);
-    const double vx = S[s] + 0.5 * P.dt * (F1[s] + f.x), vy = S[P.nw + s] + 0.5 * P.dt * (F1[P.nw + s] + f.y),
-                 vz = S[2 * P.nw + s] + 0.5 * P.dt * (F1[2 * P.nw + s] + f.z);
-    const double nv = sqrt(vx * vx + vy * vy + vz * vz);
+    const Real t = (Real)step * (Real)P.dt, mu = (Real)P.mu_s, dt = (Real)P.dt;
+    const V3<Real> ba = applied_field(D, bits, t);
+    const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g);
+    const Real px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
+    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, ex.x / mu + ba.x + BTH[s],
+                                 ex.y / mu + ba.y + BTH[P.nw + s],
+                                 ex.z / mu + Real(2) * (Real)P.ku / mu * pz + ba.z + BTH[2 * P.nw + s]);
+    const Real vx = S[s] + Real(0.5) * dt * (F1[s] + f.x), vy = S[P.nw + s] + Real(0.5) * dt * (F1[P.nw + s] + f.y),
+               vz = S[2 * P.nw + s] + Real(0.5) * dt * (F1[2 * P.nw + s] + f.z);
+    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
     S[s] = vx / nv;
     S[P.nw + s] = vy / nv;
     S[2 * P.nw + s] = vz / nv;
 }
 
-__device__ __forceinline__ bool evolved(const MsDev &P, const int *grain, long long q, int ox) {
-    const int cx = (int)(q % P.ncx);
-    return grain[q] >= 0 && (cx < ox || cx >= ox + P.wx);
-}
-
-// Per cell at t_n: the laser temperature at the cell centre and m_e(T, |B_app|).
-__global__ void k_mm_prep(double *me, double *Tq, MsDev P, ReplicaDev D, double t, double Bm) {
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q >= P.nc) return;
-    const long long cx = q % P.ncx, cy = (q / P.ncx) % P.ncy;
+// Per magnetic cell at time t (FP64): the laser temperature at the cell centre, m_e(T, |B_app|)
+// starting from the cell's previous m_e, and the cell's field and damping coefficients
+// 2 A(T)/Ms(T) = 2 A0 m_e / Ms0, 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0, alpha = lambda (1 - T/3T_C)
+// with T held in [0, T_C], stored in the arithmetic of the state.  A cell whose temperature
+// and field magnitude equal those of its last solve (Bm == Bm_last, T == Tq) keeps its values:
+// far from the spot T is the ambient temperature to the last bit.
+template <typename Real>
+__global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, MsDev P, ReplicaDev D, double t,
+                          double Bm, double Bm_last) {
+    int cx, cy, cz;
+    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    const int q = cell_at(P, cx, cy, cz);
+    if (grain[q] < 0) return;
     const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
+    if (Bm == Bm_last && T == Tq[q]) return;
     Tq[q] = T;
-    me[q] = me_root(P.T_C, T, P.mu_s, Bm);
+    const double e = me_root(P.T_C, T, P.mu_s, Bm, me[q]);
+    me[q] = e;
+    double cex = 2.0 * P.A0 * e * e / (P.Ms0 * e), cK = 2.0 * P.K0 * e * e * e / (P.Ms0 * e);
+    if (!(e > 0.0)) cex = cK = 0.0;
+    const double Tc = fmax(fmin(T, P.T_C), 0.0);
+    coef[q] = (Real)cex;
+    coef[P.nc + q] = (Real)cK;
+    coef[2 * P.nc + q] = (Real)(P.lambda * (1.0 - Tc / (3.0 * P.T_C)));
 }
 
 // One RK4 stage on the evolved cells: K = dm/dt at the stage values Vin, acc += w K and
 // Vout = m + c dt K (the next stage's values).  Cells that are not evolved keep m in both
 // stage buffers.
-__global__ void k_mm_stage(const double *Vin, double *Vout, double *acc, const double *m, const double *me,
-                           const double *Tq, const int *grain, MsDev P, int ox, double bx, double by, double bz,
-                           double c, double w, int first) {
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q >= P.nc || !evolved(P, grain, q, ox)) return;
-    const long long cx = q % P.ncx, cy = (q / P.ncx) % P.ncy, cz = q / ((long long)P.ncx * P.ncy);
-    const double vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
-    double lx = 0.0, ly = 0.0, lz = 0.0;
+template <typename Real>
+__global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
+                           MsDev P, int ox, Real bx, Real by, Real bz, Real c, Real w, int first) {
+    int cx, cy, cz;
+    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    const int q = cell_at(P, cx, cy, cz);
+    if (grain[q] < 0 || (cx >= ox && cx < ox + P.wx)) return;   // only the evolved cells
+    const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
+    Real lx = 0, ly = 0, lz = 0;
     const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-    const double c2 = P.cell * P.cell;
+    const Real c2 = (Real)(P.cell * P.cell);
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
-        const long long x = cx + off[b][0], y = cy + off[b][1], z = cz + off[b][2];
+        const int x = cx + off[b][0], y = cy + off[b][1], z = cz + off[b][2];
         if (x < 0 || x >= P.ncx || y < 0 || y >= P.ncy || z < 0 || z >= P.ncz) continue;
-        const long long qn = cell_at(P, x, y, z);
+        const int qn = cell_at(P, x, y, z);
         if (grain[qn] != grain[q]) continue;
         lx += (Vin[qn] - vx) / c2;
         ly += (Vin[P.nc + qn] - vy) / c2;
         lz += (Vin[2 * P.nc + qn] - vz) / c2;
     }
-    const double e = me[q];
-    double cex = 2.0 * P.A0 * e * e / (P.Ms0 * e), cK = 2.0 * P.K0 * e * e * e / (P.Ms0 * e);
-    if (!(e > 0.0)) cex = cK = 0.0;
-    const double T = fmax(fmin(Tq[q], P.T_C), 0.0);
-    const double alpha = P.lambda * (1.0 - T / (3.0 * P.T_C));
-    const double3 k = rhs(P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz + cK * vz + bz);
-    const double a0 = first ? 0.0 : acc[q], a1 = first ? 0.0 : acc[P.nc + q], a2 = first ? 0.0 : acc[2 * P.nc + q];
+    const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
+    const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz + cK * vz + bz);
+    const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
+               a2 = first ? Real(0) : acc[2 * P.nc + q];
     acc[q] = a0 + w * k.x;
     acc[P.nc + q] = a1 + w * k.y;
     acc[2 * P.nc + q] = a2 + w * k.z;
-    Vout[q] = m[q] + c * P.dt * k.x;
-    Vout[P.nc + q] = m[P.nc + q] + c * P.dt * k.y;
-    Vout[2 * P.nc + q] = m[2 * P.nc + q] + c * P.dt * k.z;
+    const Real dt = (Real)P.dt;
+    Vout[q] = m[q] + c * dt * k.x;
+    Vout[P.nc + q] = m[P.nc + q] + c * dt * k.y;
+    Vout[2 * P.nc + q] = m[2 * P.nc + q] + c * dt * k.z;
 }
 
-__global__ void k_mm_final(double *m, const double *acc, const int *grain, MsDev P, int ox) {
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q >= P.nc || !evolved(P, grain, q, ox)) return;
-    const double vx = m[q] + P.dt / 6.0 * acc[q], vy = m[P.nc + q] + P.dt / 6.0 * acc[P.nc + q],
-                 vz = m[2 * P.nc + q] + P.dt / 6.0 * acc[2 * P.nc + q];
-    const double nv = sqrt(vx * vx + vy * vy + vz * vz);
+template <typename Real>
+__global__ void k_mm_final(Real *m, const Real *acc, const int *grain, MsDev P, int ox) {
+    int cx, cy, cz;
+    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    const int q = cell_at(P, cx, cy, cz);
+    if (grain[q] < 0 || (cx >= ox && cx < ox + P.wx)) return;
+    const Real h6 = (Real)P.dt / Real(6);
+    const Real vx = m[q] + h6 * acc[q], vy = m[P.nc + q] + h6 * acc[P.nc + q], vz = m[2 * P.nc + q] + h6 * acc[2 * P.nc + q];
+    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
     m[q] = vx / nv;
     m[P.nc + q] = vy / nv;
     m[2 * P.nc + q] = vz / nv;
 }
 
 // Sites move back by one cell column (the last column is thermalised afterwards).
-__global__ void k_ms_shift(double *Snew, const double *Sold, MsDev P) {
+template <typename Real>
+__global__ void k_ms_shift(Real *Snew, const Real *Sold, MsDev P) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= P.nw) return;
     const int i = (int)(s % P.nxw);
-    for (int d = 0; d < 3; ++d) Snew[d * P.nw + s] = i + P.r < P.nxw ? Sold[d * P.nw + s + P.r] : 0.0;
+    for (int d = 0; d < 3; ++d) Snew[d * P.nw + s] = i + P.r < P.nxw ? Sold[d * P.nw + s + P.r] : Real(0);
 }
 
-// Thermalisation of the sites of cell columns [cx0, cx1): a spin in the cone of half-angle
-// theta_max(m_e(T_cell, |B_app|)) around the cell's m, polar angle u0 theta_max and azimuth
+// Thermalisation of the sites of cell columns [cx0, cx1) (FP64 arithmetic): a spin in the cone
+// of half-angle theta_max(m_e) around the cell's m, polar angle u0 theta_max and azimuth
 // 2 pi u1 from e1 = (z x m)/|z x m| (or (x x m)/|x x m| when |m_z| >= 0.9), e2 = m x e1, with
 // u0, u1 from Philox4x32-10 (key = seed, counter = (site low, site high, event low,
 // event high | 2^31)).
-__global__ void k_ms_thermalise(double *S, const double *m, const int *grain, MsDev P, ReplicaDev D, int ox, int cx0,
-                                int cx1, double t, double Bm, unsigned long long event) {
+template <typename Real>
+__global__ void k_ms_thermalise(Real *S, const Real *m, const double *me, const int *grain, MsDev P, int ox, int cx0,
+                                int cx1, unsigned long long event) {
     const long long ncolsites = (long long)(cx1 - cx0) * P.r;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= ncolsites * P.nyw * P.nzw) return;
     const int i = (cx0 - ox) * P.r + (int)(idx % ncolsites);
     const int j = (int)((idx / ncolsites) % P.nyw), k = (int)(idx / (ncolsites * P.nyw));
     const long long s = i + P.nxw * (j + (long long)P.nyw * k);
-    const long long q = cell_at(P, ox + i / P.r, j / P.r, k / P.r);
+    const int q = cell_at(P, ox + i / P.r, j / P.r, k / P.r);
     const double mx = m[q], my = m[P.nc + q], mz = m[2 * P.nc + q];
     if (grain[q] < 0 || (mx == 0.0 && my == 0.0 && mz == 0.0)) {
-        S[s] = S[P.nw + s] = S[2 * P.nw + s] = 0.0;
+        S[s] = S[P.nw + s] = S[2 * P.nw + s] = Real(0);
         return;
     }
-    const long long cx = q % P.ncx, cy = (q / P.ncx) % P.ncy;
-    const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
-    const double thm = theta_max(me_root(P.T_C, T, P.mu_s, Bm));
+    const double thm = theta_max(me[q]);
     const unsigned long long X = (unsigned long long)ox * P.r + i, NX = (unsigned long long)P.ncx * P.r;
     const unsigned long long site = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * k);
     const uint4 x = philox10(make_uint4((unsigned)site, (unsigned)(site >> 32), (unsigned)event,
@@ -331,33 +383,43 @@ __global__ void k_ms_thermalise(double *S, const double *m, const int *grain, Ms
     e1x /= r; e1y /= r; e1z /= r;
     const double e2x = my * e1z - mz * e1y, e2y = mz * e1x - mx * e1z, e2z = mx * e1y - my * e1x;
     const double a1 = sin(th) * cos(ph), a2 = sin(th) * sin(ph), a3 = cos(th);
-    S[s] = a1 * e1x + a2 * e2x + a3 * mx;
-    S[P.nw + s] = a1 * e1y + a2 * e2y + a3 * my;
-    S[2 * P.nw + s] = a1 * e1z + a2 * e2z + a3 * mz;
+    S[s] = (Real)(a1 * e1x + a2 * e2x + a3 * mx);
+    S[P.nw + s] = (Real)(a1 * e1y + a2 * e2y + a3 * my);
+    S[2 * P.nw + s] = (Real)(a1 * e1z + a2 * e2z + a3 * mz);
 }
 
-// AoS (host layout) <-> component planes
-__global__ void k_aos_to_planes(const double *src, double *dst, long long n) {
+// AoS FP64 (host layout) <-> component planes in the state's arithmetic
+template <typename Real>
+__global__ void k_aos_to_planes(const double *src, Real *dst, long long n) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= n) return;
-    for (int d = 0; d < 3; ++d) dst[d * n + s] = src[3 * s + d];
+    for (int d = 0; d < 3; ++d) dst[d * n + s] = (Real)src[3 * s + d];
 }
 
-__global__ void k_planes_to_aos(const double *src, double *dst, long long n) {
+template <typename Real>
+__global__ void k_planes_to_aos(const Real *src, double *dst, long long n) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= n) return;
-    for (int d = 0; d < 3; ++d) dst[3 * s + d] = src[d * n + s];
+    for (int d = 0; d < 3; ++d) dst[3 * s + d] = (double)src[d * n + s];
+}
+
+__global__ void k_fill(double *v, double x, long long n) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) v[q] = x;
 }
 
 // Zero the cells that are non-magnetic.
-__global__ void k_zero_void_cells(double *m, const int *grain, long long nc) {
+template <typename Real>
+__global__ void k_zero_void_cells(Real *m, const int *grain, long long nc) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= nc || grain[q] >= 0) return;
-    m[q] = m[nc + q] = m[2 * nc + q] = 0.0;
+    m[q] = m[nc + q] = m[2 * nc + q] = Real(0);
 }
 
 constexpr int BLK = 256;
 inline unsigned nblk(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
+inline dim3 grid3(int nx, int ny, int nz) { return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 3) / 4), (unsigned)nz); }
+const dim3 BLK3(32, 4, 1);
 
 }  // namespace
 
@@ -372,9 +434,14 @@ struct hamr_ms_ctx {
     uint8_t *bits_d = nullptr;
     int *grain_d = nullptr;
     std::vector<int> grain_h;
-    double *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *me = nullptr, *Tq = nullptr;
-    double *S = nullptr, *S2 = nullptr, *Sp = nullptr, *F1 = nullptr, *BTH = nullptr;
-    double *stage = nullptr;      // AoS staging for host copies
+    int prec = HAMR_FP64;         // arithmetic of the state and the field (HAMR_FP32 / HAMR_FP64)
+    // state-precision planes: cells m, V0, V1, acc, coef [3][nc]; window S, S2, Sp, F1, BTH [3][nw]
+    void *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *coef = nullptr;
+    void *S = nullptr, *S2 = nullptr, *Sp = nullptr, *F1 = nullptr, *BTH = nullptr;
+    double *me = nullptr;         // m_e per cell (FP64)
+    double *Tq = nullptr;         // temperature of each cell's last m_e solve (NaN: none)
+    double Bm_last = NAN;         // field magnitude of the last m_e solve
+    double *stage = nullptr;      // AoS FP64 staging for host copies
     int ox = -1;                  // window column (-1: not placed)
     long long step = 0;
     long long events = 0;         // thermalisation events so far
@@ -419,16 +486,39 @@ struct MsDeviceGuard {
 };
 
 void ms_free(hamr_ms_t h) {
-    double **bufs[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->me, &h->Tq, &h->S, &h->S2, &h->Sp, &h->F1, &h->BTH, &h->stage};
-    for (double **b : bufs)
+    void **bufs[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef, &h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
+    for (void **b : bufs)
         if (*b) {
             cudaFree(*b);
             *b = nullptr;
         }
+    if (h->me) cudaFree(h->me);
+    if (h->Tq) cudaFree(h->Tq);
+    if (h->stage) cudaFree(h->stage);
+    h->me = nullptr;
+    h->Tq = nullptr;
+    h->stage = nullptr;
     if (h->grain_d) cudaFree(h->grain_d);
     if (h->bits_d) cudaFree(h->bits_d);
     h->grain_d = nullptr;
     h->bits_d = nullptr;
+}
+
+// FP32 copies of the driver parameters (read by the FP32 kernels)
+void set_driver_floats(ReplicaDev &D) {
+    D.fT_amb = (float)D.T_amb;
+    D.fdT = (float)D.dT;
+    D.fc_fwhm = (float)D.c_fwhm;
+    D.fx0 = (float)D.x0;
+    D.fy0 = (float)D.y0;
+    D.fvx = (float)D.vx;
+    D.fvy = (float)D.vy;
+    D.fB0 = (float)D.B0;
+    for (int k = 0; k < 3; ++k) D.fdir[k] = (float)D.dir[k];
+    D.fbit_len = (float)D.bit_len;
+    D.framp_len = (float)D.ramp_len;
+    D.fhead_x0 = (float)D.head_x0;
+    D.fhead_v = (float)D.head_v;
 }
 
 // B_app(t) = B0 s(t) dir, with the polarity s(t) of the bit pattern computed as on the device
@@ -458,19 +548,27 @@ double field_magnitude_host(const hamr_ms_t h, double t) {
     return sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
 }
 
+template <typename Real>
 int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
     const long long n = (long long)(cx1 - cx0) * h->P.r * h->P.nyw * h->P.nzw;
     if (n <= 0) return HAMR_OK;
-    k_ms_thermalise<<<nblk(n), BLK, 0, h->stream>>>(h->S, h->m, h->grain_d, h->P, h->D, h->ox, cx0, cx1, t,
-                                                    field_magnitude_host(h, t), (unsigned long long)h->events);
+    // m_e(T) of every cell at t, then the cone of each thermalised site from its cell's m_e
+    const double Bm = field_magnitude_host(h, t);
+    k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, h->P.ncz), BLK3, 0, h->stream>>>(
+        h->me, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, Bm, h->Bm_last);
+    h->Bm_last = Bm;
+    k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
+                                                          h->ox, cx0, cx1, (unsigned long long)h->events);
     MSCK(h, cudaGetLastError());
     h->events += 1;
     return HAMR_OK;
 }
 
+template <typename Real>
 int ms_average(hamr_ms_t h, int cx0, int ncol) {
     const long long n = (long long)ncol * h->P.ncy * h->P.ncz;
-    k_ms_average<<<nblk(n), BLK, 0, h->stream>>>(h->m, h->S, h->grain_d, h->P, h->ox, cx0, ncol);
+    k_ms_average<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->m, (const Real *)h->S, h->grain_d, h->P, h->ox, cx0,
+                                                       ncol);
     MSCK(h, cudaGetLastError());
     return HAMR_OK;
 }
@@ -483,43 +581,86 @@ int ms_target(const hamr_ms_t h, double t) {
 }
 
 // One coupled step n -> n+1 (stages 1-3 of the file header).
+template <typename Real>
 int ms_step(hamr_ms_t h) {
     const MsDev &P = h->P;
     cudaStream_t st = h->stream;
-    int rc = ms_average(h, h->ox, P.wx);
+    int rc = ms_average<Real>(h, h->ox, P.wx);
     if (rc) return rc;
-    k_ms_predict<<<nblk(P.nw), BLK, 0, st>>>(h->S, h->Sp, h->F1, h->BTH, h->m, h->grain_d, P, h->D, h->bits_d, h->ox,
-                                             h->step);
-    k_ms_correct<<<nblk(P.nw), BLK, 0, st>>>(h->S, h->Sp, h->F1, h->BTH, h->m, h->grain_d, P, h->D, h->bits_d, h->ox,
-                                             h->step);
+    Real *S = (Real *)h->S, *Sp = (Real *)h->Sp, *F1 = (Real *)h->F1, *BTH = (Real *)h->BTH, *m = (Real *)h->m;
+    const dim3 gw = grid3(P.nxw, P.nyw, P.nzw);
+#define MS_HEUN(RT)                                                                                              \
+    do {                                                                                                         \
+        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, h->bits_d, h->ox, h->step); \
+        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, h->bits_d, h->ox, h->step); \
+    } while (0)
+    switch (P.r) {
+        case 1: MS_HEUN(1); break;
+        case 2: MS_HEUN(2); break;
+        case 4: MS_HEUN(4); break;
+        default: MS_HEUN(0); break;
+    }
+#undef MS_HEUN
     MSCK(h, cudaGetLastError());
     const double t = (double)h->step * P.dt;
     double B[3];
     applied_host(h, t, B);
-    k_mm_prep<<<nblk(P.nc), BLK, 0, st>>>(h->me, h->Tq, P, h->D, t, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
-    MSCK(h, cudaMemcpyAsync(h->V0, h->m, sizeof(double) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
-    MSCK(h, cudaMemcpyAsync(h->V1, h->m, sizeof(double) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
-    const double cst[4] = {0.5, 0.5, 1.0, 0.0}, wst[4] = {1.0, 2.0, 2.0, 1.0};
+    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
+    const double Bm = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, Bm, h->Bm_last);
+    h->Bm_last = Bm;
+    MSCK(h, cudaMemcpyAsync(h->V0, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
+    MSCK(h, cudaMemcpyAsync(h->V1, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
+    const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
     for (int s = 0; s < 4; ++s) {
-        const double *vin = (s & 1) ? h->V1 : h->V0;
-        double *vout = (s & 1) ? h->V0 : h->V1;
-        k_mm_stage<<<nblk(P.nc), BLK, 0, st>>>(vin, vout, h->acc, h->m, h->me, h->Tq, h->grain_d, P, h->ox, B[0], B[1],
-                                               B[2], cst[s], wst[s], s == 0);
+        const Real *vin = (const Real *)((s & 1) ? h->V1 : h->V0);
+        Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
+        k_mm_stage<Real><<<gc, BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m, (const Real *)h->coef, h->grain_d, P, h->ox,
+                                              (Real)B[0], (Real)B[1], (Real)B[2], cst[s], wst[s], s == 0);
     }
-    k_mm_final<<<nblk(P.nc), BLK, 0, st>>>(h->m, h->acc, h->grain_d, P, h->ox);
+    k_mm_final<Real><<<gc, BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox);
     MSCK(h, cudaGetLastError());
     h->step += 1;
     return HAMR_OK;
 }
 
+template <typename Real>
 int ms_shift_forward(hamr_ms_t h, double t) {
-    int rc = ms_average(h, h->ox, 1);
+    int rc = ms_average<Real>(h, h->ox, 1);
     if (rc) return rc;
-    k_ms_shift<<<nblk(h->P.nw), BLK, 0, h->stream>>>(h->S2, h->S, h->P);
+    k_ms_shift<Real><<<nblk(h->P.nw), BLK, 0, h->stream>>>((Real *)h->S2, (const Real *)h->S, h->P);
     MSCK(h, cudaGetLastError());
     std::swap(h->S, h->S2);
     h->ox += 1;
-    return ms_thermalise(h, h->ox + h->P.wx - 1, h->ox + h->P.wx, t);
+    return ms_thermalise<Real>(h, h->ox + h->P.wx - 1, h->ox + h->P.wx, t);
+}
+
+// host FP64 AoS (already in h->stage) -> state planes, and back
+int ms_to_planes(hamr_ms_t h, void *dst, long long n) {
+    if (h->prec == HAMR_FP64)
+        k_aos_to_planes<double><<<nblk(n), BLK, 0, h->stream>>>(h->stage, (double *)dst, n);
+    else
+        k_aos_to_planes<float><<<nblk(n), BLK, 0, h->stream>>>(h->stage, (float *)dst, n);
+    MSCK(h, cudaGetLastError());
+    return HAMR_OK;
+}
+
+int ms_from_planes(hamr_ms_t h, const void *src, long long n) {
+    if (h->prec == HAMR_FP64)
+        k_planes_to_aos<double><<<nblk(n), BLK, 0, h->stream>>>((const double *)src, h->stage, n);
+    else
+        k_planes_to_aos<float><<<nblk(n), BLK, 0, h->stream>>>((const float *)src, h->stage, n);
+    MSCK(h, cudaGetLastError());
+    return HAMR_OK;
+}
+
+int ms_zero_void(hamr_ms_t h) {
+    if (h->prec == HAMR_FP64)
+        k_zero_void_cells<double><<<nblk(h->P.nc), BLK, 0, h->stream>>>((double *)h->m, h->grain_d, h->P.nc);
+    else
+        k_zero_void_cells<float><<<nblk(h->P.nc), BLK, 0, h->stream>>>((float *)h->m, h->grain_d, h->P.nc);
+    MSCK(h, cudaGetLastError());
+    return HAMR_OK;
 }
 
 }  // namespace
@@ -535,15 +676,21 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     const long long nc = (long long)d->ncx * d->ncy * d->ncz;
     const long long nw = (long long)d->wx * d->ratio * (long long)d->ncy * d->ratio * (long long)d->ncz * d->ratio;
     if (nc > (1LL << 31) || nw > (1LL << 31)) return msfail(nullptr, HAMR_ERR_ARG, "mesh or window too large");
+    // launch grids: (x / 32, y / 4, z) blocks
+    if ((long long)d->ncy * d->ratio > 4 * 65535LL || (long long)d->ncz * d->ratio > 65535LL)
+        return msfail(nullptr, HAMR_ERR_ARG, "at most 262140 sites across the track and 65535 through it");
     const double vals[] = {d->cell, d->mu_s, d->gamma, d->dt, d->T_C, d->Ms0};
     for (double v : vals)
         if (!(v > 0) || !isfinite(v))
             return msfail(nullptr, HAMR_ERR_ARG, "cell, mu_s, gamma, dt, T_C and Ms0 must be positive");
     if (!isfinite(d->J) || !isfinite(d->ku) || !(d->lambda >= 0) || !isfinite(d->A0) || !isfinite(d->K0))
         return msfail(nullptr, HAMR_ERR_ARG, "J, ku, A0, K0 must be finite and lambda >= 0");
+    if (d->precision != HAMR_FP32 && d->precision != HAMR_FP64)
+        return msfail(nullptr, HAMR_ERR_ARG, "precision must be HAMR_FP32 or HAMR_FP64");
     hamr_ms_t h = new (std::nothrow) hamr_ms_ctx();
     if (!h) return msfail(nullptr, HAMR_ERR_OOM, "host allocation failed");
     h->device = d->device;
+    h->prec = d->precision;
     MsDeviceGuard dg(h->device);
     MsDev &P = h->P;
     P.ncx = d->ncx; P.ncy = d->ncy; P.ncz = d->ncz; P.r = d->ratio; P.wx = d->wx;
@@ -557,6 +704,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     P.key0 = (unsigned)d->seed;
     P.key1 = (unsigned)(d->seed >> 32);
     h->D.dir[2] = 1.0;
+    set_driver_floats(h->D);
     if (d->stream) {
         h->stream = (cudaStream_t)d->stream;
     } else {
@@ -567,20 +715,26 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
         }
         h->own_stream = true;
     }
-    double **bufs3c[] = {&h->m, &h->V0, &h->V1, &h->acc};
+    const size_t el = h->prec == HAMR_FP64 ? sizeof(double) : sizeof(float);
+    void **bufs3c[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef};
     cudaError_t e = cudaSuccess;
-    for (double **b : bufs3c)
-        if (e == cudaSuccess) e = cudaMalloc((void **)b, sizeof(double) * 3 * nc);
+    for (void **b : bufs3c)
+        if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->Tq, sizeof(double) * nc);
-    double **bufs3w[] = {&h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
-    for (double **b : bufs3w)
-        if (e == cudaSuccess) e = cudaMalloc((void **)b, sizeof(double) * 3 * nw);
+    void **bufs3w[] = {&h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
+    for (void **b : bufs3w)
+        if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nw);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->stage, sizeof(double) * 3 * (nw > nc ? nw : nc));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->grain_d, sizeof(int) * nc);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->m, 0, sizeof(double) * 3 * nc, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, sizeof(double) * 3 * nw, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->m, 0, el * 3 * nc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, el * 3 * nw, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->grain_d, 0, sizeof(int) * nc, h->stream);
+    if (e == cudaSuccess) {
+        k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->me, 1.0, nc);
+        k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->Tq, NAN, nc);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         ms_free(h);
@@ -601,8 +755,8 @@ int hamr_ms_set_grain_map(hamr_ms_t h, const int32_t *cell_grain) {
     MsDeviceGuard dg(h->device);
     h->grain_h.assign(cell_grain, cell_grain + h->P.nc);
     MSCK(h, cudaMemcpyAsync(h->grain_d, h->grain_h.data(), sizeof(int) * h->P.nc, cudaMemcpyHostToDevice, h->stream));
-    k_zero_void_cells<<<nblk(h->P.nc), BLK, 0, h->stream>>>(h->m, h->grain_d, h->P.nc);
-    MSCK(h, cudaGetLastError());
+    int rc = ms_zero_void(h);
+    if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     h->grains_set = true;
     return HAMR_OK;
@@ -620,6 +774,7 @@ int hamr_ms_set_temperature_profile(hamr_ms_t h, double T_amb, double T_peak, do
     D.dT = fwhm > 0 ? T_peak - T_amb : 0.0;
     D.c_fwhm = fwhm > 0 ? -4.0 * log(2.0) / (fwhm * fwhm) : 0.0;
     D.x0 = x0; D.y0 = y0; D.vx = vx; D.vy = vy;
+    set_driver_floats(D);
     return HAMR_OK;
 }
 
@@ -638,6 +793,7 @@ int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], cons
     D.n_bits = n_bits;
     D.bits_off = 0;
     D.bit_len = bit_len; D.ramp_len = ramp_len; D.head_x0 = head_x0; D.head_v = head_v;
+    set_driver_floats(D);
     h->bits_h.assign(bits, bits + n_bits);
     if (h->bits_d) cudaFree(h->bits_d);
     h->bits_d = nullptr;
@@ -655,9 +811,9 @@ int hamr_ms_set_cells(hamr_ms_t h, const double *m) {
         if (!isfinite(m[q])) return msfail(h, HAMR_ERR_ARG, "non-finite cell value at %lld", q / 3);
     MsDeviceGuard dg(h->device);
     MSCK(h, cudaMemcpyAsync(h->stage, m, sizeof(double) * 3 * h->P.nc, cudaMemcpyHostToDevice, h->stream));
-    k_aos_to_planes<<<nblk(h->P.nc), BLK, 0, h->stream>>>(h->stage, h->m, h->P.nc);
-    k_zero_void_cells<<<nblk(h->P.nc), BLK, 0, h->stream>>>(h->m, h->grain_d, h->P.nc);
-    MSCK(h, cudaGetLastError());
+    int rc = ms_to_planes(h, h->m, h->P.nc);
+    if (!rc) rc = ms_zero_void(h);
+    if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     h->cells_set = true;
     return HAMR_OK;
@@ -671,7 +827,9 @@ int hamr_ms_set_window(hamr_ms_t h, int32_t x0_cells) {
     if (!h->cells_set) return msfail(h, HAMR_ERR_STATE, "set the cells (hamr_ms_set_cells) before the window");
     MsDeviceGuard dg(h->device);
     h->ox = x0_cells;
-    int rc = ms_thermalise(h, h->ox, h->ox + h->P.wx, (double)h->step * h->P.dt);
+    const double t = (double)h->step * h->P.dt;
+    int rc = h->prec == HAMR_FP64 ? ms_thermalise<double>(h, h->ox, h->ox + h->P.wx, t)
+                                  : ms_thermalise<float>(h, h->ox, h->ox + h->P.wx, t);
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
@@ -682,8 +840,8 @@ int hamr_ms_set_moments(hamr_ms_t h, const double *S) {
     if (h->ox < 0) return msfail(h, HAMR_ERR_STATE, "place the window (hamr_ms_set_window) first");
     MsDeviceGuard dg(h->device);
     MSCK(h, cudaMemcpyAsync(h->stage, S, sizeof(double) * 3 * h->P.nw, cudaMemcpyHostToDevice, h->stream));
-    k_aos_to_planes<<<nblk(h->P.nw), BLK, 0, h->stream>>>(h->stage, h->S, h->P.nw);
-    MSCK(h, cudaGetLastError());
+    int rc = ms_to_planes(h, h->S, h->P.nw);
+    if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
 }
@@ -694,16 +852,17 @@ int hamr_ms_steps(hamr_ms_t h, int64_t n_steps, int32_t follow) {
     if (h->ox < 0) return msfail(h, HAMR_ERR_STATE, "place the window (hamr_ms_set_window) first");
     MsDeviceGuard dg(h->device);
     for (int64_t s = 0; s < n_steps; ++s) {
-        int rc = ms_step(h);
+        int rc = h->prec == HAMR_FP64 ? ms_step<double>(h) : ms_step<float>(h);
         if (rc) return rc;
         if (follow) {
             const double t = (double)h->step * h->P.dt;
             const int target = ms_target(h, t);
             while (h->ox < target)
-                if ((rc = ms_shift_forward(h, t))) return rc;
+                if ((rc = h->prec == HAMR_FP64 ? ms_shift_forward<double>(h, t) : ms_shift_forward<float>(h, t)))
+                    return rc;
         }
     }
-    int rc = ms_average(h, h->ox, h->P.wx);
+    int rc = h->prec == HAMR_FP64 ? ms_average<double>(h, h->ox, h->P.wx) : ms_average<float>(h, h->ox, h->P.wx);
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
@@ -712,8 +871,8 @@ int hamr_ms_steps(hamr_ms_t h, int64_t n_steps, int32_t follow) {
 int hamr_ms_read_cells(hamr_ms_t h, double *m_out) {
     if (!h || !m_out) return h ? msfail(h, HAMR_ERR_ARG, "m_out is NULL") : HAMR_ERR_ARG;
     MsDeviceGuard dg(h->device);
-    k_planes_to_aos<<<nblk(h->P.nc), BLK, 0, h->stream>>>(h->m, h->stage, h->P.nc);
-    MSCK(h, cudaGetLastError());
+    int rc = ms_from_planes(h, h->m, h->P.nc);
+    if (rc) return rc;
     MSCK(h, cudaMemcpyAsync(m_out, h->stage, sizeof(double) * 3 * h->P.nc, cudaMemcpyDeviceToHost, h->stream));
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
@@ -722,8 +881,8 @@ int hamr_ms_read_cells(hamr_ms_t h, double *m_out) {
 int hamr_ms_read_moments(hamr_ms_t h, double *S_out) {
     if (!h || !S_out) return h ? msfail(h, HAMR_ERR_ARG, "S_out is NULL") : HAMR_ERR_ARG;
     MsDeviceGuard dg(h->device);
-    k_planes_to_aos<<<nblk(h->P.nw), BLK, 0, h->stream>>>(h->S, h->stage, h->P.nw);
-    MSCK(h, cudaGetLastError());
+    int rc = ms_from_planes(h, h->S, h->P.nw);
+    if (rc) return rc;
     MSCK(h, cudaMemcpyAsync(S_out, h->stage, sizeof(double) * 3 * h->P.nw, cudaMemcpyDeviceToHost, h->stream));
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;

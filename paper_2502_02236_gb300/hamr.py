@@ -75,7 +75,7 @@ class MsDesc(ctypes.Structure):
         ("Ms0", ctypes.c_double), ("A0", ctypes.c_double), ("K0", ctypes.c_double),
         ("lambda_", ctypes.c_double), ("T_C", ctypes.c_double),
         ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("precision", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -383,16 +383,17 @@ def sllg_heun_step_noalloc(dims, S_in, S_out, *, grain=None, step=0, periodic=(F
 
 class Multiscale:
     """One hamr_ms_t handle: the multiscale write window (an atomistic simple-cubic window
-    in a micromagnetic track, FP64).  Cell arrays are (ncx*ncy*ncz, 3), window spins
+    in a micromagnetic track, FP64 or FP32).  Cell arrays are (ncx*ncy*ncz, 3), window spins
     (nxw*nyw*nzw, 3), x fastest."""
 
     def __init__(self, ncx, ncy, ncz, cell, ratio, wx, *, J, mu_s, ku, Ms0, A0, K0, lam, T_C,
-                 dt=1e-16, gamma=GAMMA, seed=1, device=None, stream="torch"):
+                 dt=1e-16, gamma=GAMMA, seed=1, precision="fp64", device=None, stream="torch"):
         L = lib()
         d = MsDesc()
         d.ncx, d.ncy, d.ncz, d.cell, d.ratio, d.wx = ncx, ncy, ncz, cell, ratio, wx
         d.J, d.mu_s, d.ku, d.Ms0, d.A0, d.K0 = J, mu_s, ku, Ms0, A0, K0
         d.lambda_, d.T_C, d.gamma, d.dt, d.seed = lam, T_C, gamma, dt, int(seed)
+        d.precision = PRECISION[precision]
         tdev, tstream = _torch_current()
         d.device = tdev if device is None else device
         d.stream = tstream if stream == "torch" else stream
