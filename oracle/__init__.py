@@ -129,6 +129,7 @@ def lib():
         L.orc_ms_target.restype = i32
         L.orc_ms_run.argtypes = [vp, i64, i32]
         L.orc_ms_run.restype = ctypes.c_int
+        L.orc_ms_read_track.argtypes = [vp, d, d, i32, i32, i32, vp, vp]
         _lib = L
     return _lib
 
@@ -462,3 +463,12 @@ class MsOracle:
     def run(self, n_steps, follow=False):
         if lib().orc_ms_run(self._h, int(n_steps), int(bool(follow))) != 0:
             raise MemoryError("oracle step allocation failed")
+
+    def read_track(self, x_start, bit_len, n_bits, cy0=0, cy1=None):
+        """Mean m_z of the magnetic cells of each bit window and the bits it reads as."""
+        cy1 = self.p.ncy if cy1 is None else cy1
+        sig = np.zeros(max(n_bits, 1))
+        bits = np.zeros(max(n_bits, 1), dtype=np.uint8)
+        lib().orc_ms_read_track(self._h, float(x_start), float(bit_len), int(n_bits), int(cy0), int(cy1),
+                                _dp(sig), _dp(bits))
+        return sig[:n_bits], bits[:n_bits]

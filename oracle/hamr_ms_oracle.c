@@ -487,3 +487,30 @@ int orc_ms_run(orc_ms *c, int64_t n_steps, int32_t follow)
     average_cells(c, c->ox, c->ox + c->p.wx);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Read-back of the written track: a stand-in for the read head (Sec. III), whose
+ * tunnel-junction model is not part of the paper.  Bit b covers the cells whose centre x lies
+ * in [x_start + b L, x_start + (b + 1) L) and whose row cy lies in [cy0, cy1), all layers; its
+ * signal is the mean m_z over the magnetic cells there (0 when there are none), and it reads
+ * as 1 when the signal is negative (a '1' is written along -z). */
+void orc_ms_read_track(const orc_ms *c, double x_start, double bit_len, int32_t n_bits, int32_t cy0, int32_t cy1,
+                       double *signal, uint8_t *bits)
+{
+    for (int32_t b = 0; b < n_bits; ++b) {
+        double sum = 0.0;
+        int64_t count = 0;
+        for (int32_t cz = 0; cz < c->p.ncz; ++cz)
+            for (int32_t cy = cy0; cy < cy1; ++cy)
+                for (int32_t cx = 0; cx < c->p.ncx; ++cx) {
+                    double x = (cx + 0.5) * c->p.cell;
+                    if (!(x >= x_start + b * bit_len && x < x_start + (b + 1) * bit_len)) continue;
+                    int64_t q = cell_index(&c->p, cx, cy, cz);
+                    if (c->grain[q] < 0) continue;
+                    sum += c->m[3 * q + 2];
+                    count += 1;
+                }
+        signal[b] = count > 0 ? sum / (double)count : 0.0;
+        if (bits) bits[b] = signal[b] < 0.0 ? 1 : 0;
+    }
+}

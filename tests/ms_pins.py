@@ -323,6 +323,34 @@ def check_shift_moves_spins():
         assert np.abs(m[0, cy, 3] - s / np.linalg.norm(s)).max() < 1e-9
 
 
+def check_read_track():
+    """Read-back: cells set to +z / -z by bit regions read back as the written pattern with
+    signals of exactly +1 / -1; non-magnetic cells and rows outside the band do not count;
+    a bit window with no magnetic cell reads 0."""
+    ncx, ncy, ncz, L = 40, 6, 2, 5
+    p = o.MsParams(ncx, ncy, ncz, 1e-9, 1, 4, J=J_SC)
+    grain = np.zeros(ncx * ncy * ncz, np.int32)
+    g3 = grain.reshape(ncz, ncy, ncx)
+    g3[:, :, 17] = -1
+    g3[:, :, 30:35] = -1                          # bit 6 has no magnetic cell
+    pattern = [0, 1, 1, 0, 1, 0, 0, 1]
+    m = np.zeros((ncz, ncy, ncx, 3))
+    for b, v in enumerate(pattern):
+        m[:, :, b * L:(b + 1) * L, 2] = -1.0 if v else 1.0
+    m[:, 0, :, 2] = 1.0                           # a row outside the band, along +z everywhere
+    m[:, :, 17, 2] = -1.0                         # a non-magnetic cell (set to 0 by set_cells)
+    O = o.MsOracle(p, grain)
+    O.set_cells(m.reshape(-1, 3))
+    sig, bits = O.read_track(0.0, L * 1e-9, len(pattern), cy0=1, cy1=ncy)
+    want = np.array([-1.0 if v else 1.0 for v in pattern])
+    want[6] = 0.0
+    assert np.array_equal(sig, want), sig
+    assert list(bits) == [v if b != 6 else 0 for b, v in enumerate(pattern)]
+    # the band including row 0 averages it in: bit 1 reads -1 over 5 rows and +1 over 1
+    sig2, _ = O.read_track(0.0, L * 1e-9, 2, cy0=0, cy1=ncy)
+    assert abs(sig2[1] - (-5 + 1) / 6) < 1e-15
+
+
 def check_window_target():
     """The window is centred on the laser spot and stays on the track."""
     p = o.MsParams(20, 1, 1, 1e-9, 4, 6, J=J_SC, x0=10.2e-9, vx=1.0)
@@ -338,5 +366,5 @@ FAST_CHECKS = [
     check_theta_max_printed_values, check_cone_distribution, check_eq6_average_brute_force,
     check_uniform_state_stationary_through_shifts, check_isolated_cell_llg, check_mm_standing_spin_wave,
     check_ratio_one_window_matches_atomistic_lattice, check_full_window_equals_atomistic_oracle,
-    check_shift_moves_spins, check_window_target,
+    check_shift_moves_spins, check_window_target, check_read_track,
 ]

@@ -40,6 +40,9 @@ MUTANTS = [
     ("window anisotropy factor", "B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2]",
      "B[2] = ex[2] / p->mu_s + p->ku / p->mu_s * Si[2]"),
     ("window target off by half a window", "floor(xc / p->cell - 0.5 * p->wx + 0.5)", "floor(xc / p->cell + 0.5)"),
+    ("read-back counts non-magnetic cells", "if (c->grain[q] < 0) continue;\n                    sum +=",
+     "sum +="),
+    ("read-back bit sign", "bits[b] = signal[b] < 0.0 ? 1 : 0;", "bits[b] = signal[b] > 0.0 ? 1 : 0;"),
 ]
 
 
