@@ -352,6 +352,16 @@ int hamr_ms_steps(hamr_ms_t h, int64_t n_steps, int32_t follow);
 /* Reads m (3 ncx ncy ncz doubles) or the window spins (3 nxw nyw nzw doubles). */
 int hamr_ms_read_cells(hamr_ms_t h, double *m_out);
 int hamr_ms_read_moments(hamr_ms_t h, double *S_out);
+/* Read-back of the written track, a stand-in for the read head of Sec. III (its tunnel-
+ * junction model is not part of the paper).  Bit b (0 <= b < n_bits) covers the cells whose
+ * centre x lies in [x_start + b bit_len, x_start + (b + 1) bit_len) and whose row lies in
+ * [cy0, cy1), all layers; signal[b] = mean m_z over its magnetic cells (window cells count
+ * with their Eq. 6 directions; 0 when there is no magnetic cell), bits[b] = 1 where the signal
+ * is negative (a '1' is written along -z), else 0.  signal: caller-owned n_bits doubles;
+ * bits: caller-owned n_bits bytes, or NULL.  ARG on bit_len <= 0, an empty or out-of-range
+ * row band, or a NULL signal. */
+int hamr_ms_read_track(hamr_ms_t h, double x_start, double bit_len, int32_t n_bits, int32_t cy0, int32_t cy1,
+                       double *signal, uint8_t *bits);
 /* Window column (-1 before placement) and completed steps; either pointer may be NULL. */
 int hamr_ms_get_window(hamr_ms_t h, int32_t *x0_cells, int64_t *step);
 const char *hamr_ms_last_error(hamr_ms_t h);

@@ -416,6 +416,43 @@ __global__ void k_zero_void_cells(Real *m, const int *grain, long long nc) {
     m[q] = m[nc + q] = m[2 * nc + q] = Real(0);
 }
 
+// Read-back: block b sums m_z over the magnetic cells whose centre x lies in
+// [x_start + b L, x_start + (b + 1) L) and whose row lies in [cy0, cy1); each thread takes a
+// fixed stride of the band and the block adds the partial sums in a fixed tree, so the result
+// does not depend on scheduling.  signal[b] = mean m_z (0 without magnetic cells).
+template <typename Real>
+__global__ void k_ms_read_track(const Real *m, const int *grain, MsDev P, double x_start, double bit_len, int cy0,
+                                int cy1, double *signal) {
+    __shared__ double ssum[256];
+    __shared__ long long scnt[256];
+    const int b = blockIdx.x;
+    const double lo = x_start + b * bit_len, hi = x_start + (b + 1) * bit_len;
+    const long long nband = (long long)P.ncx * (cy1 - cy0) * P.ncz;
+    double sum = 0.0;
+    long long cnt = 0;
+    for (long long idx = threadIdx.x; idx < nband; idx += blockDim.x) {
+        const int cx = (int)(idx % P.ncx);
+        const double x = (cx + 0.5) * P.cell;
+        if (!(x >= lo && x < hi)) continue;
+        const int cy = cy0 + (int)((idx / P.ncx) % (cy1 - cy0)), cz = (int)(idx / ((long long)P.ncx * (cy1 - cy0)));
+        const int q = cell_at(P, cx, cy, cz);
+        if (grain[q] < 0) continue;
+        sum += (double)m[2 * P.nc + q];
+        cnt += 1;
+    }
+    ssum[threadIdx.x] = sum;
+    scnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            ssum[threadIdx.x] += ssum[threadIdx.x + w];
+            scnt[threadIdx.x] += scnt[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) signal[b] = scnt[0] > 0 ? ssum[0] / (double)scnt[0] : 0.0;
+}
+
 constexpr int BLK = 256;
 inline unsigned nblk(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 inline dim3 grid3(int nx, int ny, int nz) { return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 3) / 4), (unsigned)nz); }
@@ -892,6 +929,31 @@ int hamr_ms_get_window(hamr_ms_t h, int32_t *x0_cells, int64_t *step) {
     if (!h) return HAMR_ERR_ARG;
     if (x0_cells) *x0_cells = h->ox;
     if (step) *step = h->step;
+    return HAMR_OK;
+}
+
+int hamr_ms_read_track(hamr_ms_t h, double x_start, double bit_len, int32_t n_bits, int32_t cy0, int32_t cy1,
+                       double *signal, uint8_t *bits) {
+    if (!h) return HAMR_ERR_ARG;
+    if (n_bits < 0 || !isfinite(x_start) || !(bit_len > 0) || !isfinite(bit_len) || cy0 < 0 || cy1 > h->P.ncy ||
+        cy0 >= cy1)
+        return msfail(h, HAMR_ERR_ARG, "bad read-back window (bit_len > 0, 0 <= cy0 < cy1 <= ncy)");
+    if (n_bits > 0 && !signal) return msfail(h, HAMR_ERR_ARG, "signal is NULL");
+    if ((long long)n_bits > 3 * (h->P.nw > h->P.nc ? h->P.nw : h->P.nc))
+        return msfail(h, HAMR_ERR_ARG, "too many bits (%d)", n_bits);
+    if (n_bits == 0) return HAMR_OK;
+    MsDeviceGuard dg(h->device);
+    if (h->prec == HAMR_FP64)
+        k_ms_read_track<double><<<n_bits, 256, 0, h->stream>>>((const double *)h->m, h->grain_d, h->P, x_start, bit_len,
+                                                              cy0, cy1, h->stage);
+    else
+        k_ms_read_track<float><<<n_bits, 256, 0, h->stream>>>((const float *)h->m, h->grain_d, h->P, x_start, bit_len,
+                                                             cy0, cy1, h->stage);
+    MSCK(h, cudaGetLastError());
+    MSCK(h, cudaMemcpyAsync(signal, h->stage, sizeof(double) * n_bits, cudaMemcpyDeviceToHost, h->stream));
+    MSCK(h, cudaStreamSynchronize(h->stream));
+    if (bits)
+        for (int32_t b = 0; b < n_bits; ++b) bits[b] = signal[b] < 0.0 ? 1 : 0;
     return HAMR_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "hamr_sllg_heun_step_noalloc", "hamr_inject_wait_timeout",
     "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
     "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
-    "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window",
+    "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window", "hamr_ms_read_track",
     "hamr_ms_last_error", "hamr_ms_destroy",
 ]
 NOALLOC_MAX_SITES = 131072
@@ -130,6 +130,7 @@ def lib():
             "hamr_ms_read_cells": [vp, vp],
             "hamr_ms_read_moments": [vp, vp],
             "hamr_ms_get_window": [vp, vp, vp],
+            "hamr_ms_read_track": [vp, d, d, i32, i32, i32, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -398,6 +399,7 @@ class Multiscale:
         d.device = tdev if device is None else device
         d.stream = tstream if stream == "torch" else stream
         self.n_cells = ncx * ncy * ncz
+        self.ncy = ncy
         self.window_dims = (wx * ratio, ncy * ratio, ncz * ratio)
         self.n_window = int(np.prod(self.window_dims))
         h = ctypes.c_void_p()
@@ -471,6 +473,16 @@ class Multiscale:
         S = np.zeros((self.n_window, 3))
         self._ck(lib().hamr_ms_read_moments(self._h, _p(S)))
         return S
+
+    def read_track(self, x_start, bit_len, n_bits, cy0=0, cy1=None):
+        """Mean m_z of the magnetic cells in each bit window of the track (rows cy0..cy1-1)
+        and the bits it reads as (1 where negative)."""
+        cy1 = self.ncy if cy1 is None else cy1
+        sig = np.zeros(max(int(n_bits), 1))
+        bits = np.zeros(max(int(n_bits), 1), dtype=np.uint8)
+        self._ck(lib().hamr_ms_read_track(self._h, float(x_start), float(bit_len), int(n_bits), int(cy0), int(cy1),
+                                          _p(sig), _p(bits)))
+        return sig[:n_bits], bits[:n_bits]
 
     def window(self):
         ox = ctypes.c_int32()

@@ -125,6 +125,40 @@ def test_full_track_two_steps_matches_oracle(prec):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_read_track_matches_oracle(prec):
+    """Read-back of the track: a written pattern of +z / -z bit regions reads back exactly; after
+    a coupled run the per-bit signals match the oracle's."""
+    w = I.multiscale_track(ncx=60, ncy=8, ncz=2, cell=1e-9, ratio=2, wx=8, grain_d=5e-9, seed=25, v=0.0,
+                           x_spot=30.2e-9)
+    p, O, G = pair(w, prec)
+    L, pattern = 6e-9, [0, 1, 1, 0, 1, 0, 0, 1, 1, 0]
+    n = w["ncx"] * w["ncy"] * w["ncz"]
+    m = np.zeros((w["ncz"], w["ncy"], w["ncx"], 3))
+    for b, v in enumerate(pattern):
+        m[:, :, b * 6:(b + 1) * 6, 2] = -1.0 if v else 1.0
+    m = I.mask_void(m.reshape(n, 3), w["grain"])
+    with G:
+        G.set_cells(m)
+        O.set_cells(m)
+        sig, bits = G.read_track(0.0, L, len(pattern), 1, 7)
+        osig, obits = O.read_track(0.0, L, len(pattern), 1, 7)
+        assert list(bits) == pattern == list(obits)
+        assert np.abs(sig - osig).max() < 1e-12
+        # after a coupled run with the window over the track
+        m2 = tilted_cells(w)
+        G.set_cells(m2)
+        O.set_cells(m2)
+        G.set_window(11)
+        O.set_window(11)
+        G.steps(50)
+        O.run(50)
+        sig, bits = G.read_track(0.0, L, len(pattern), 0, 8)
+        osig, obits = O.read_track(0.0, L, len(pattern), 0, 8)
+        assert np.abs(sig - osig).max() < TOL[prec], np.abs(sig - osig).max()
+
+
+@pytest.mark.gpu
 def test_call_order_and_arguments():
     w = I.multiscale_track(ncx=12, ncy=3, ncz=2, cell=1e-9, ratio=2, wx=4, grain_d=3e-9, seed=24)
     with Multiscale(12, 3, 2, 1e-9, 2, 4, J=w["J"], mu_s=w["mu_s"], ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"],
@@ -147,3 +181,7 @@ def test_call_order_and_arguments():
         with pytest.raises(HamrError) as e:
             G.set_grain_map(bad)
         assert e.value.code == ERR_ARG
+        for args in ((0.0, 0.0, 3), (0.0, 1e-9, 3, 2, 2), (0.0, 1e-9, 3, 0, 4)):
+            with pytest.raises(HamrError) as e:
+                G.read_track(*args)
+            assert e.value.code == ERR_ARG
