@@ -96,3 +96,40 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hamr, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         hamr.lib()
+
+
+def _ms_desc(**over):
+    from paper_2502_02236_gb300.hamr import MsDesc
+    d = MsDesc()
+    d.ncx, d.ncy, d.ncz, d.cell, d.ratio, d.wx = 20, 4, 2, 1e-9, 2, 6
+    d.J, d.mu_s, d.ku = 6.7e-21, 2.78e-23, 1e-22
+    d.Ms0, d.A0, d.K0 = 1.78e6, 1.34e-11, 6.4e6
+    d.lambda_, d.T_C, d.gamma, d.dt, d.seed = 0.1, 700.0, 1.76e11, 1e-16, 1
+    d.precision = 1
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("bad", [
+    dict(ncx=0), dict(ncy=-1), dict(ratio=0), dict(wx=0), dict(wx=21), dict(cell=0.0), dict(mu_s=0.0),
+    dict(dt=-1e-16), dict(T_C=0.0), dict(Ms0=0.0), dict(lambda_=-0.1), dict(J=float("nan")), dict(precision=2),
+    dict(ncz=70000, ratio=1),
+])
+def test_multiscale_create_rejects_bad_descriptor(hlib, bad):
+    """The multiscale window's descriptor is checked before any device work."""
+    d = _ms_desc(**bad)
+    h = ctypes.c_void_p()
+    assert hlib.hamr_ms_create(ctypes.byref(h), ctypes.byref(d)) == -1
+    assert not h.value
+    assert hlib.hamr_ms_last_error(None)
+
+
+def test_multiscale_null_arguments(hlib):
+    d = _ms_desc()
+    assert hlib.hamr_ms_create(None, ctypes.byref(d)) == -1
+    h = ctypes.c_void_p()
+    assert hlib.hamr_ms_create(ctypes.byref(h), None) == -1
+    for f, args in (("hamr_ms_steps", (1, 0)), ("hamr_ms_set_window", (0,)), ("hamr_ms_read_cells", (None,)),
+                    ("hamr_ms_set_cells", (None,))):
+        assert getattr(hlib, f)(None, *args) == -1
