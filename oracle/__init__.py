@@ -55,6 +55,8 @@ class OrcMsParams(ctypes.Structure):
         ("Ms0", ctypes.c_double), ("A0", ctypes.c_double), ("K0", ctypes.c_double),
         ("lambda_", ctypes.c_double), ("T_C", ctypes.c_double),
         ("drv", OrcParams),
+        ("profile", ctypes.c_int32), ("prof_wz", ctypes.c_double), ("prof_dz", ctypes.c_double),
+        ("prof_Bx0", ctypes.c_double), ("prof_wx", ctypes.c_double), ("prof_dx", ctypes.c_double),
     ]
 
 
@@ -130,6 +132,7 @@ def lib():
         L.orc_ms_run.argtypes = [vp, i64, i32]
         L.orc_ms_run.restype = ctypes.c_int
         L.orc_ms_read_track.argtypes = [vp, d, d, i32, i32, i32, vp, vp]
+        L.orc_ms_field.argtypes = [MP, d, d, vp]
         _lib = L
     return _lib
 
@@ -359,8 +362,10 @@ class MsParams:
                  T_C=None, Ms0=None, A0=None, K0=None, dt=1e-16, gamma=C_GAMMA, seed=1,
                  T_amb=0.0, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0,
                  B0=0.0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0, ramp_len=0.0,
-                 head_x0=0.0, head_v=0.0):
+                 head_x0=0.0, head_v=0.0, profile=None):
         self.ncx, self.ncy, self.ncz = int(ncx), int(ncy), int(ncz)
+        # head profile: dict(wz=, dz=, Bx0=, wx=, dx=) or None for a uniform field
+        self.profile = dict(profile) if profile else None
         self.cell, self.ratio, self.wx = float(cell), int(ratio), int(wx)
         a = self.cell / self.ratio
         self.a = a
@@ -392,6 +397,10 @@ class MsParams:
         s.Ms0, s.A0, s.K0 = self.Ms0, self.A0, self.K0
         s.lambda_, s.T_C = self.lam, self.T_C
         s.drv = self.drv.struct()
+        if self.profile:
+            s.profile = 1
+            s.prof_wz, s.prof_dz = self.profile["wz"], self.profile["dz"]
+            s.prof_Bx0, s.prof_wx, s.prof_dx = self.profile["Bx0"], self.profile["wx"], self.profile["dx"]
         self._keep = self.drv
         return s
 
@@ -399,6 +408,14 @@ class MsParams:
 def ms_alpha(p, T):
     s = p.struct()
     return lib().orc_ms_alpha(ctypes.byref(s), float(T))
+
+
+def ms_field(p, x, t):
+    """The write field at track position x and time t."""
+    s = p.struct()
+    B = np.zeros(3)
+    lib().orc_ms_field(ctypes.byref(s), float(x), float(t), _dp(B))
+    return B
 
 
 def ms_target(p, t):

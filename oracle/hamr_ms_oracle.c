@@ -14,7 +14,8 @@
  * id (-1 = non-magnetic) is shared by every site inside it.
  *
  * One coupled step n -> n+1 (t_n = n dt).  Drivers (laser temperature, write field) are
- * frozen at t_n for the whole step.
+ * frozen at t_n for the whole step; the write field is uniform or follows the head with tanh
+ * profiles along the track (orc_ms_field).
  *   1. Eq. 6: each cell inside the window takes the direction of the sum of its
  *      atomistic spins (0 for a non-magnetic cell).  The micromagnetic exchange of the
  *      neighbouring cells then sees the average atomistic direction (Sec. II).
@@ -52,6 +53,10 @@ typedef struct {
     double lambda;          /* atomistic damping; micromagnetic alpha(T) = lambda (1 - T/3T_C) */
     double T_C;             /* Curie temperature [K] */
     orc_params drv;         /* gamma, dt, seed, laser spot and write field (other fields unused) */
+    int32_t profile;        /* 0: spatially uniform write field; 1: tanh profiles along the track */
+    double prof_wz, prof_dz; /* width and offset from the head of the profile of B0 dir [m] */
+    double prof_Bx0;        /* amplitude of the in-plane (x) component [T] */
+    double prof_wx, prof_dx; /* its width and offset from the head [m] */
 } orc_ms_params;
 
 typedef struct {
@@ -138,6 +143,24 @@ void orc_cone_sample(const double e3[3], double theta_max, uint64_t seed, uint64
     double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2], e3[0] * e1[1] - e3[1] * e1[0]};
     double a1 = sin(th) * cos(ph), a2 = sin(th) * sin(ph), a3 = cos(th);
     for (int d = 0; d < 3; ++d) out[d] = a1 * e1[d] + a2 * e2[d] + a3 * e3[d];
+}
+
+/* The write field at track position x and time t (Sec. III, Fig. 2).  Uniform: B0 s(t) dir.
+ * With the head profile: each component is a tanh step along the track that follows the
+ * head at x_h(t) = head_x0 + head_v t,
+ *   B(x, t) = B0 s(t) dir P(x - x_h - dz, wz) + Bx0 s(t) P(x - x_h - dx, wx) x,
+ *   P(u, w) = (1 - tanh(u / w)) / 2,
+ * full under the pole upstream and zero downstream, with s(t) the bit polarity. */
+void orc_ms_field(const orc_ms_params *p, double x, double t, double B[3])
+{
+    orc_applied_field(&p->drv, t, B);
+    if (!p->profile) return;
+    double s = orc_field_polarity(&p->drv, t);
+    double xh = p->drv.head_x0 + p->drv.head_v * t;
+    double Pz = 0.5 * (1.0 - tanh((x - xh - p->prof_dz) / p->prof_wz));
+    double Px = 0.5 * (1.0 - tanh((x - xh - p->prof_dx) / p->prof_wx));
+    for (int d = 0; d < 3; ++d) B[d] *= Pz;
+    B[0] += p->prof_Bx0 * s * Px;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -242,9 +265,6 @@ static void thermalise(orc_ms *c, int32_t cx0, int32_t cx1, double t, uint64_t e
 {
     const int r = c->p.ratio;
     const int64_t nxw = (int64_t)c->p.wx * r, nyw = (int64_t)c->p.ncy * r, nzw = (int64_t)c->p.ncz * r;
-    double B[3];
-    orc_applied_field(&c->p.drv, t, B);
-    double Bm = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
     for (int64_t k = 0; k < nzw; ++k)
         for (int64_t j = 0; j < nyw; ++j)
             for (int64_t i = (int64_t)(cx0 - c->ox) * r; i < (int64_t)(cx1 - c->ox) * r; ++i) {
@@ -255,6 +275,9 @@ static void thermalise(orc_ms *c, int32_t cx0, int32_t cx1, double t, uint64_t e
                     Si[0] = Si[1] = Si[2] = 0.0;
                     continue;
                 }
+                double B[3];
+                orc_ms_field(&c->p, (q % c->p.ncx + 0.5) * c->p.cell, t, B);
+                double Bm = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
                 double mr = orc_me(c->p.T_C, cell_temperature(c, q, t), c->p.mu_s, Bm);
                 orc_cone_sample(mq, orc_theta_max(mr), c->p.drv.seed, track_site(c, i, j, k), event, Si);
             }
@@ -336,8 +359,6 @@ static int atom_step(orc_ms *c)
     double *f1 = (double *)calloc(3 * (size_t)n, sizeof(double));
     double *Sp = (double *)calloc(3 * (size_t)n, sizeof(double));
     if (!Bth || !f1 || !Sp) { free(Bth); free(f1); free(Sp); return -1; }
-    double Bapp[3];
-    orc_applied_field(&p->drv, t, Bapp);
     /* thermal field, field at S and predictor */
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < n; ++s) {
@@ -349,7 +370,8 @@ static int atom_step(orc_ms *c)
         double xi[3];
         orc_thermal_normals(p->drv.seed, track_site(c, i, j, k), (uint64_t)c->step, xi);
         for (int d = 0; d < 3; ++d) Bth[3 * s + d] = sigma * xi[d];
-        double ex[3], B[3];
+        double ex[3], B[3], Bapp[3];
+        orc_ms_field(p, ((double)c->ox * r + i + 0.5) * a, t, Bapp);
         site_exchange(c, c->S, i, j, k, g, ex);
         const double *Si = c->S + 3 * s;
         B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
@@ -367,7 +389,8 @@ static int atom_step(orc_ms *c)
         int64_t i = s % nxw, j = (s / nxw) % nyw, k = s / (nxw * nyw);
         int32_t g = c->grain[site_cell(c, i, j, k)];
         if (g < 0) continue;
-        double ex[3], B[3], f2[3];
+        double ex[3], B[3], f2[3], Bapp[3];
+        orc_ms_field(p, ((double)c->ox * r + i + 0.5) * a, t, Bapp);
         site_exchange(c, Sp, i, j, k, g, ex);
         const double *Spi = Sp + 3 * s;
         B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
@@ -388,7 +411,7 @@ static int atom_step(orc_ms *c)
 /* Micromagnetic RK4 step (stage 3) */
 
 /* dm/dt of cell q for the stage values V, with per-cell m_e and T at t_n. */
-static void mm_rate(const orc_ms *c, const double *V, int64_t q, double me, double T, const double Bapp[3],
+static void mm_rate(const orc_ms *c, const double *V, int64_t q, double me, double T, const double *Bapp,
                     double k[3])
 {
     const orc_ms_params *p = &c->p;
@@ -422,10 +445,11 @@ static int mm_step(orc_ms *c)
     double *me = (double *)malloc(sizeof(double) * (size_t)nc);
     double *T = (double *)malloc(sizeof(double) * (size_t)nc);
     if (!V || !K || !acc || !me || !T) { free(V); free(K); free(acc); free(me); free(T); return -1; }
-    double Bapp[3];
-    orc_applied_field(&p->drv, t, Bapp);
-    double Bm = sqrt(Bapp[0] * Bapp[0] + Bapp[1] * Bapp[1] + Bapp[2] * Bapp[2]);
+    double *Bq = (double *)malloc(sizeof(double) * 3 * (size_t)nc);
+    if (!Bq) { free(V); free(K); free(acc); free(me); free(T); return -1; }
     for (int64_t q = 0; q < nc; ++q) {
+        orc_ms_field(p, (q % p->ncx + 0.5) * p->cell, t, Bq + 3 * q);
+        double Bm = sqrt(Bq[3 * q] * Bq[3 * q] + Bq[3 * q + 1] * Bq[3 * q + 1] + Bq[3 * q + 2] * Bq[3 * q + 2]);
         T[q] = cell_temperature(c, q, t);
         me[q] = orc_me(p->T_C, T[q], p->mu_s, Bm);
     }
@@ -436,7 +460,7 @@ static int mm_step(orc_ms *c)
 #pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < nc; ++q) {
             if (!ORC_EVOLVED(q)) continue;
-            mm_rate(c, V, q, me[q], T[q], Bapp, K + 3 * q);
+            mm_rate(c, V, q, me[q], T[q], Bq + 3 * q, K + 3 * q);
         }
         for (int64_t q = 0; q < nc; ++q) {
             if (!ORC_EVOLVED(q)) continue;
@@ -454,7 +478,7 @@ static int mm_step(orc_ms *c)
         for (int d = 0; d < 3; ++d) c->m[3 * q + d] = v[d] / nv;
     }
 #undef ORC_EVOLVED
-    free(V); free(K); free(acc); free(me); free(T);
+    free(V); free(K); free(acc); free(me); free(T); free(Bq);
     return 0;
 }
 

@@ -351,6 +351,61 @@ def check_read_track():
     assert abs(sig2[1] - (-5 + 1) / 6) < 1e-15
 
 
+PROFILE = dict(wz=3e-9, dz=2e-9, Bx0=0.3, wx=2e-9, dx=-1e-9)
+
+
+def check_head_profile_shape():
+    """Write field with the head profile (a reading of the tanh profiles of Sec. III, Fig. 2):
+    the full field B0 s(t) dir and Bx0 s(t) x far upstream of the head, half of each at its
+    offset from the head, none far downstream; the polarity s(t) of the bit pattern flips both
+    components; without the profile the field is uniform."""
+    kw = dict(J=J_SC, B0=0.8, direction=(0, 0, -1), head_x0=10e-9, head_v=1e3, bits=[0, 1], bit_len=15e-9,
+              ramp_len=1e-12)
+    p = o.MsParams(30, 1, 1, 1e-9, 1, 2, profile=PROFILE, **kw)
+    xh = 10e-9
+    B = o.ms_field(p, xh - 1e-6, 0.0)
+    assert np.allclose(B, [0.3, 0.0, -0.8], atol=1e-12)
+    assert abs(o.ms_field(p, xh + 2e-9, 0.0)[2] + 0.4) < 1e-15
+    assert abs(o.ms_field(p, xh - 1e-9, 0.0)[0] - 0.15) < 1e-15
+    assert np.allclose(o.ms_field(p, xh + 1e-6, 0.0), 0.0, atol=1e-15)
+    # the head has moved into bit 1 (polarity -1) at t = 10 ns
+    t = 10e-9
+    assert o.field_polarity(p.drv, t) == -1.0
+    assert np.allclose(o.ms_field(p, xh + 1e3 * t - 1e-6, t), [-0.3, 0.0, 0.8], atol=1e-12)
+    pu = o.MsParams(30, 1, 1, 1e-9, 1, 2, **kw)
+    for x in (0.0, 12e-9, 1e-6):
+        assert np.array_equal(o.ms_field(pu, x, 0.0), o.applied_field(pu.drv, 0.0))
+
+
+def _rotate(v, axis, ang):
+    k = axis / np.linalg.norm(axis)
+    return v * math.cos(ang) + np.cross(k, v) * math.sin(ang) + k * (k @ v) * (1 - math.cos(ang))
+
+
+def check_isolated_cell_and_site_in_head_profile():
+    """An isolated micromagnetic cell and an isolated window site (no magnetic neighbour, no
+    anisotropy, no damping, T = 0) precess about the local profile field B(x) at gamma |B(x)|:
+    both sides of the window evaluate the field where they sit."""
+    dt, n = 2e-16, 500
+    p = o.MsParams(12, 1, 1, A, 1, 2, J=J_SC, ku=0.0, lam=0.0, dt=dt, T_amb=0.0, B0=1.0, direction=(0, 0, 1),
+                   head_x0=6 * A, head_v=0.0, profile=dict(wz=2 * A, dz=0.0, Bx0=0.6, wx=3 * A, dx=A))
+    grain = np.full(12, -1, np.int32)
+    grain[3] = 0          # a cell outside the window
+    grain[8] = 1          # the window's one site (window at columns 8, 9)
+    O = o.MsOracle(p, grain)
+    m0 = np.zeros((12, 3))
+    m0[3] = m0[8] = (math.sin(0.5), 0.0, math.cos(0.5))
+    O.set_cells(m0)
+    O.set_window(8)
+    O.set_moments(np.array([[math.sin(0.5), 0.0, math.cos(0.5)], [0.0, 0.0, 0.0]]))
+    O.run(n)
+    t = n * dt
+    for x, got in (((3 + 0.5) * A, O.cells()[3]), ((8 + 0.5) * A, O.moments()[0])):
+        B = o.ms_field(p, x, 0.0)
+        want = _rotate(np.array([math.sin(0.5), 0.0, math.cos(0.5)]), B, G * np.linalg.norm(B) * t)
+        assert np.linalg.norm(got - want) < 1e-8, (x, got, want)
+
+
 def check_window_target():
     """The window is centred on the laser spot and stays on the track."""
     p = o.MsParams(20, 1, 1, 1e-9, 4, 6, J=J_SC, x0=10.2e-9, vx=1.0)
@@ -366,5 +421,6 @@ FAST_CHECKS = [
     check_theta_max_printed_values, check_cone_distribution, check_eq6_average_brute_force,
     check_uniform_state_stationary_through_shifts, check_isolated_cell_llg, check_mm_standing_spin_wave,
     check_ratio_one_window_matches_atomistic_lattice, check_full_window_equals_atomistic_oracle,
-    check_shift_moves_spins, check_window_target, check_read_track,
+    check_shift_moves_spins, check_window_target, check_read_track, check_head_profile_shape,
+    check_isolated_cell_and_site_in_head_profile,
 ]

@@ -43,6 +43,13 @@ MUTANTS = [
     ("read-back counts non-magnetic cells", "if (c->grain[q] < 0) continue;\n                    sum +=",
      "sum +="),
     ("read-back bit sign", "bits[b] = signal[b] < 0.0 ? 1 : 0;", "bits[b] = signal[b] > 0.0 ? 1 : 0;"),
+    ("head profile upside down", "double Pz = 0.5 * (1.0 - tanh(", "double Pz = 0.5 * (1.0 + tanh("),
+    ("in-plane component without polarity", "B[0] += p->prof_Bx0 * s * Px;", "B[0] += p->prof_Bx0 * Px;"),
+    ("window ignores the head profile",
+     "orc_ms_field(p, ((double)c->ox * r + i + 0.5) * a, t, Bapp);\n        site_exchange(c, c->S,",
+     "orc_applied_field(&p->drv, t, Bapp);\n        site_exchange(c, c->S,"),
+    ("cells ignore the head profile", "orc_ms_field(p, (q % p->ncx + 0.5) * p->cell, t, Bq + 3 * q);",
+     "orc_applied_field(&p->drv, t, Bq + 3 * q);"),
 ]
 
 
