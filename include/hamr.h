@@ -335,6 +335,15 @@ int hamr_ms_set_temperature_profile(hamr_ms_t h, double T_amb, double T_peak, do
                                     double vx, double vy);
 int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], const uint8_t *bits, int32_t n_bits,
                                double bit_len, double ramp_len, double head_x0, double head_v);
+/* Spatial profile of the write field along the track (Sec. III, Fig. 2, where the head
+ * field is drawn as tanh profiles of its out-of-plane and in-plane components; the paper gives
+ * no formula, this is the reading): with wz > 0 the field at x is
+ *   B0 s(t) dir P(x - x_h(t) - dz, wz) + Bx0 s(t) P(x - x_h(t) - dx, wx) x,
+ *   P(u, w) = (1 - tanh(u / w)) / 2,   x_h(t) = head_x0 + head_v t,
+ * full under the pole upstream of the head and zero downstream, in both regions and in the
+ * m_e(T) law.  wz <= 0 restores the spatially uniform field B0 s(t) dir.  ARG on non-finite
+ * values or wx <= 0. */
+int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, double wx, double dx);
 /* Micromagnetic directions m (3 ncx ncy ncz doubles, AoS; copied; non-magnetic cells are
  * set to 0).  ARG on non-finite values. */
 int hamr_ms_set_cells(hamr_ms_t h, const double *m);

@@ -42,6 +42,16 @@ struct MsDev {
     double lambda, T_C, gamma, dt;
     double sig0;               // sqrt(2 lambda kB / (gamma mu_s dt)): sigma_i = sig0 sqrt(T_i)
     unsigned key0, key1;       // Philox key = seed (low, high)
+    int profile;               // write field: 0 uniform, 1 tanh profiles following the head
+    double pwz, pdz, pBx0, pwx, pdx;  // profile widths, offsets from the head [m], in-plane amplitude [T]
+};
+
+// The write field at one step, from the host: B0 s(t) dir, Bx0 s(t) and the head position.
+template <typename Real>
+struct Field {
+    Real bx, by, bz;   // B0 s(t) dir
+    Real bxs;          // Bx0 s(t)
+    Real xh;           // head position x_h(t)
 };
 
 template <typename Real>
@@ -66,13 +76,15 @@ __device__ __forceinline__ double temp_at(const ReplicaDev &D, double x, double 
 __device__ __forceinline__ float temp_at(const ReplicaDev &D, float x, float y, float t) {
     return temperature_f(D, x, y, t);
 }
-__device__ __forceinline__ V3<double> applied_field(const ReplicaDev &D, const uint8_t *bits, double t) {
-    const double s = D.B0 * field_polarity(D, bits, t);
-    return {s * D.dir[0], s * D.dir[1], s * D.dir[2]};
-}
-__device__ __forceinline__ V3<float> applied_field(const ReplicaDev &D, const uint8_t *bits, float t) {
-    const float s = D.fB0 * field_polarity_f(D, bits, t);
-    return {s * D.fdir[0], s * D.fdir[1], s * D.fdir[2]};
+// The write field at track position x (Sec. III, Fig. 2): uniform B0 s(t) dir, or with the
+// head profile B0 s(t) dir P(x - x_h - dz, wz) + Bx0 s(t) P(x - x_h - dx, wx) x with
+// P(u, w) = (1 - tanh(u / w)) / 2.
+template <typename Real>
+__device__ __forceinline__ V3<Real> field_at(const MsDev &P, const Field<Real> &F, Real x) {
+    if (!P.profile) return {F.bx, F.by, F.bz};
+    const Real Pz = Real(0.5) * (Real(1) - tanh((x - F.xh - (Real)P.pdz) / (Real)P.pwz));
+    const Real Px = Real(0.5) * (Real(1) - tanh((x - F.xh - (Real)P.pdx) / (Real)P.pwx));
+    return {F.bx * Pz + F.bxs * Px, F.by * Pz, F.bz * Pz};
 }
 
 __device__ __forceinline__ double langevin(double x) {
@@ -200,7 +212,7 @@ __device__ __forceinline__ V3<Real> exchange(const MsDev &P, const Real *V, cons
 
 template <typename Real, int RT>
 __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const Real *m, const int *grain, MsDev P,
-                             ReplicaDev D, const uint8_t *bits, int ox, long long step) {
+                             ReplicaDev D, Field<Real> F, int ox, long long step) {
     int i, j, k;
     if (!coords(P.nxw, P.nyw, i, j, k)) return;
     const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
@@ -220,7 +232,7 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
     BTH[s] = bthx;
     BTH[P.nw + s] = bthy;
     BTH[2 * P.nw + s] = bthz;
-    const V3<Real> ba = applied_field(D, bits, t);
+    const V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * a);
     const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g);
     const Real sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
     const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, ex.x / mu + ba.x + bthx,
@@ -238,14 +250,14 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
 
 template <typename Real, int RT>
 __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real *BTH, const Real *m, const int *grain,
-                             MsDev P, ReplicaDev D, const uint8_t *bits, int ox, long long step) {
+                             MsDev P, Field<Real> F, int ox, long long step) {
     int i, j, k;
     if (!coords(P.nxw, P.nyw, i, j, k)) return;
     const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
     const int g = grain[cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k))];
     if (g < 0) return;
-    const Real t = (Real)step * (Real)P.dt, mu = (Real)P.mu_s, dt = (Real)P.dt;
-    const V3<Real> ba = applied_field(D, bits, t);
+    const Real mu = (Real)P.mu_s, dt = (Real)P.dt;
+    const V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * (Real)P.a);
     const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g);
     const Real px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
     const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, ex.x / mu + ba.x + BTH[s],
@@ -267,13 +279,15 @@ __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real
 // far from the spot T is the ambient temperature to the last bit.
 template <typename Real>
 __global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, MsDev P, ReplicaDev D, double t,
-                          double Bm, double Bm_last) {
+                          Field<double> F, double Bm_last) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
     const int q = cell_at(P, cx, cy, cz);
     if (grain[q] < 0) return;
     const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
-    if (Bm == Bm_last && T == Tq[q]) return;
+    const V3<double> B = field_at(P, F, (cx + 0.5) * P.cell);
+    const double Bm = sqrt(B.x * B.x + B.y * B.y + B.z * B.z);
+    if (!P.profile && Bm == Bm_last && T == Tq[q]) return;
     Tq[q] = T;
     const double e = me_root(P.T_C, T, P.mu_s, Bm, me[q]);
     me[q] = e;
@@ -290,7 +304,7 @@ __global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, 
 // stage buffers.
 template <typename Real>
 __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Real bx, Real by, Real bz, Real c, Real w, int first) {
+                           MsDev P, int ox, Field<Real> F, Real c, Real w, int first) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
     const int q = cell_at(P, cx, cy, cz);
@@ -310,6 +324,8 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
         lz += (Vin[2 * P.nc + qn] - vz) / c2;
     }
     const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
+    const V3<Real> ba = field_at(P, F, (Real)((cx + 0.5) * P.cell));
+    const Real bx = ba.x, by = ba.y, bz = ba.z;
     const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz + cK * vz + bz);
     const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
                a2 = first ? Real(0) : acc[2 * P.nc + q];
@@ -558,31 +574,50 @@ void set_driver_floats(ReplicaDev &D) {
     D.fhead_v = (float)D.head_v;
 }
 
-// B_app(t) = B0 s(t) dir, with the polarity s(t) of the bit pattern computed as on the device
-void applied_host(const hamr_ms_t h, double t, double B[3]) {
+// The polarity s(t) of the bit pattern, computed as on the device: linear ramp from bit b-1's
+// polarity to bit b's over the first ramp_len of bit b, 1 without a pattern.
+double polarity_host(const hamr_ms_t h, double t) {
     const ReplicaDev &D = h->D;
-    double s = 1.0;
-    if (D.n_bits > 0) {
-        const double xh = D.head_x0 + D.head_v * t;
-        const double fb = floor(xh / D.bit_len);
-        const long long b = (long long)fb;
-        const double into = xh - fb * D.bit_len;
-        auto pol = [&](long long bi) {
-            bi = bi < 0 ? 0 : (bi > D.n_bits - 1 ? D.n_bits - 1 : bi);
-            return h->bits_h[bi] ? -1.0 : 1.0;
-        };
-        double w = D.ramp_len > 0.0 ? into / D.ramp_len : 1.0;
-        w = fmin(fmax(w, 0.0), 1.0);
-        s = pol(b - 1) + (pol(b) - pol(b - 1)) * w;
-    }
-    for (int d = 0; d < 3; ++d) B[d] = D.B0 * s * D.dir[d];
+    if (D.n_bits <= 0) return 1.0;
+    const double xh = D.head_x0 + D.head_v * t;
+    const double fb = floor(xh / D.bit_len);
+    const long long b = (long long)fb;
+    const double into = xh - fb * D.bit_len;
+    auto pol = [&](long long bi) {
+        bi = bi < 0 ? 0 : (bi > D.n_bits - 1 ? D.n_bits - 1 : bi);
+        return h->bits_h[bi] ? -1.0 : 1.0;
+    };
+    double w = D.ramp_len > 0.0 ? into / D.ramp_len : 1.0;
+    w = fmin(fmax(w, 0.0), 1.0);
+    return pol(b - 1) + (pol(b) - pol(b - 1)) * w;
 }
 
-// |B_app(t)|, the field in the Langevin equation for m_e
+// B0 s(t) dir
+void applied_host(const hamr_ms_t h, double t, double B[3]) {
+    const double s = polarity_host(h, t);
+    for (int d = 0; d < 3; ++d) B[d] = h->D.B0 * s * h->D.dir[d];
+}
+
+// |B0 s(t) dir|, the uniform field's magnitude (the m_e solve of a cell is kept while this and
+// the cell's temperature are unchanged)
 double field_magnitude_host(const hamr_ms_t h, double t) {
     double B[3];
     applied_host(h, t, B);
     return sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+}
+
+// The write field of time t for the kernels: B0 s(t) dir, Bx0 s(t) and the head position
+template <typename Real>
+Field<Real> field_of(const hamr_ms_t h, double t) {
+    double B[3];
+    applied_host(h, t, B);
+    Field<Real> F;
+    F.bx = (Real)B[0];
+    F.by = (Real)B[1];
+    F.bz = (Real)B[2];
+    F.bxs = (Real)(h->P.pBx0 * polarity_host(h, t));
+    F.xh = (Real)(h->D.head_x0 + h->D.head_v * t);
+    return F;
 }
 
 template <typename Real>
@@ -592,7 +627,7 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
     // m_e(T) of every cell at t, then the cone of each thermalised site from its cell's m_e
     const double Bm = field_magnitude_host(h, t);
     k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, h->P.ncz), BLK3, 0, h->stream>>>(
-        h->me, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, Bm, h->Bm_last);
+        h->me, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last);
     h->Bm_last = Bm;
     k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
                                                           h->ox, cx0, cx1, (unsigned long long)h->events);
@@ -626,10 +661,12 @@ int ms_step(hamr_ms_t h) {
     if (rc) return rc;
     Real *S = (Real *)h->S, *Sp = (Real *)h->Sp, *F1 = (Real *)h->F1, *BTH = (Real *)h->BTH, *m = (Real *)h->m;
     const dim3 gw = grid3(P.nxw, P.nyw, P.nzw);
-#define MS_HEUN(RT)                                                                                              \
-    do {                                                                                                         \
-        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, h->bits_d, h->ox, h->step); \
-        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, h->bits_d, h->ox, h->step); \
+    const double t = (double)h->step * P.dt;
+    const Field<Real> F = field_of<Real>(h, t);
+#define MS_HEUN(RT)                                                                                          \
+    do {                                                                                                     \
+        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, F, h->ox, h->step); \
+        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, F, h->ox, h->step);       \
     } while (0)
     switch (P.r) {
         case 1: MS_HEUN(1); break;
@@ -639,12 +676,10 @@ int ms_step(hamr_ms_t h) {
     }
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
-    const double t = (double)h->step * P.dt;
-    double B[3];
-    applied_host(h, t, B);
     const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
-    const double Bm = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, Bm, h->Bm_last);
+    const double Bm = field_magnitude_host(h, t);
+    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, field_of<double>(h, t),
+                                         h->Bm_last);
     h->Bm_last = Bm;
     MSCK(h, cudaMemcpyAsync(h->V0, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
     MSCK(h, cudaMemcpyAsync(h->V1, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
@@ -653,7 +688,7 @@ int ms_step(hamr_ms_t h) {
         const Real *vin = (const Real *)((s & 1) ? h->V1 : h->V0);
         Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
         k_mm_stage<Real><<<gc, BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m, (const Real *)h->coef, h->grain_d, P, h->ox,
-                                              (Real)B[0], (Real)B[1], (Real)B[2], cst[s], wst[s], s == 0);
+                                              F, cst[s], wst[s], s == 0);
     }
     k_mm_final<Real><<<gc, BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox);
     MSCK(h, cudaGetLastError());
@@ -839,6 +874,23 @@ int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], cons
         MSCK(h, cudaMemcpyAsync(h->bits_d, h->bits_h.data(), n_bits, cudaMemcpyHostToDevice, h->stream));
         MSCK(h, cudaStreamSynchronize(h->stream));
     }
+    return HAMR_OK;
+}
+
+int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, double wx, double dx) {
+    if (!h) return HAMR_ERR_ARG;
+    if (!(wz > 0)) {
+        h->P.profile = 0;
+        return HAMR_OK;
+    }
+    if (!isfinite(Bx0) || !isfinite(wz) || !isfinite(dz) || !(wx > 0) || !isfinite(wx) || !isfinite(dx))
+        return msfail(h, HAMR_ERR_ARG, "head profile: finite values, widths > 0");
+    h->P.profile = 1;
+    h->P.pBx0 = Bx0;
+    h->P.pwz = wz;
+    h->P.pdz = dz;
+    h->P.pwx = wx;
+    h->P.pdx = dx;
     return HAMR_OK;
 }
 

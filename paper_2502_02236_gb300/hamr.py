@@ -30,6 +30,7 @@ EXPORTS = [
     "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
     "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
     "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window", "hamr_ms_read_track",
+    "hamr_ms_set_head_profile",
     "hamr_ms_last_error", "hamr_ms_destroy",
 ]
 NOALLOC_MAX_SITES = 131072
@@ -131,6 +132,7 @@ def lib():
             "hamr_ms_read_moments": [vp, vp],
             "hamr_ms_get_window": [vp, vp, vp],
             "hamr_ms_read_track": [vp, d, d, i32, i32, i32, vp, vp],
+            "hamr_ms_set_head_profile": [vp, d, d, d, d, d],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -445,6 +447,11 @@ class Multiscale:
         b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
         self._ck(lib().hamr_ms_set_field_sequence(self._h, B0, _p(dr), _p(b) if b.size else None, b.size,
                                                   bit_len, ramp_len, head_x0, head_v))
+
+    def set_head_profile(self, Bx0=0.0, wz=0.0, dz=0.0, wx=1.0, dx=0.0):
+        """tanh profiles of the write field along the track following the head (wz <= 0: a
+        spatially uniform field)."""
+        self._ck(lib().hamr_ms_set_head_profile(self._h, Bx0, wz, dz, wx, dx))
 
     def set_cells(self, m):
         m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(-1))

@@ -14,13 +14,14 @@ TOL = {"fp64": 1e-9, "fp32": 2e-4}
 PRECISIONS = ["fp64", "fp32"]
 
 
-def pair(w, precision="fp64"):
+def pair(w, precision="fp64", profile=None):
     """The oracle and the GPU handle for one multiscale input description."""
     T, F = w["T"], w["field"]
     p = orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                      ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
                      seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
-                     bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"])
+                     bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"],
+                     profile=profile)
     O = orc.MsOracle(p, w["grain"])
     G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                    ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
@@ -28,6 +29,8 @@ def pair(w, precision="fp64"):
     G.set_grain_map(w["grain"])
     G.set_temperature_profile(**T)
     G.set_field_sequence(**F)
+    if profile:
+        G.set_head_profile(**profile)
     return p, O, G
 
 
@@ -122,6 +125,30 @@ def test_full_track_two_steps_matches_oracle(prec):
         G.steps(2)
         dm, dS = compare(O, G)
         assert dm < TOL[prec] and dS < TOL[prec], (dm, dS)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_head_profile_matches_oracle(prec):
+    """The write field as tanh profiles following a moving head over a bit pattern, in both
+    regions and in m_e(T), with the window following the spot."""
+    w = I.multiscale_track(ncx=40, ncy=6, ncz=2, cell=1e-9, ratio=2, wx=8, grain_d=5e-9, seed=26, v=1.2e5,
+                           x_spot=12.013e-9)
+    w["field"].update(bit_len=4e-9, ramp_len=0.5e-9, head_x0=12.4e-9, head_v=1.2e5, B0=1.5)
+    prof = dict(Bx0=0.6, wz=3e-9, dz=1e-9, wx=2e-9, dx=-1e-9)
+    p, O, G = pair(w, prec, profile=prof)
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        ox = O.window
+        O.run(150, follow=True)
+        G.steps(150, follow=True)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], (dm, dS)
+        assert G.window()[0] == O.window >= ox + 1
+        G.set_head_profile(wz=0.0)          # back to the uniform field
+        with pytest.raises(HamrError) as e:
+            G.set_head_profile(Bx0=0.1, wz=1e-9, wx=0.0)
+        assert e.value.code == ERR_ARG
 
 
 @pytest.mark.gpu
