@@ -57,6 +57,7 @@ class OrcMsParams(ctypes.Structure):
         ("drv", OrcParams),
         ("profile", ctypes.c_int32), ("prof_wz", ctypes.c_double), ("prof_dz", ctypes.c_double),
         ("prof_Bx0", ctypes.c_double), ("prof_wx", ctypes.c_double), ("prof_dx", ctypes.c_double),
+        ("demag", ctypes.c_int32),
     ]
 
 
@@ -133,6 +134,12 @@ def lib():
         L.orc_ms_run.restype = ctypes.c_int
         L.orc_ms_read_track.argtypes = [vp, d, d, i32, i32, i32, vp, vp]
         L.orc_ms_field.argtypes = [MP, d, d, vp]
+        L.orc_newell_f.argtypes = [d, d, d]
+        L.orc_newell_f.restype = d
+        L.orc_newell_g.argtypes = [d, d, d]
+        L.orc_newell_g.restype = d
+        L.orc_demag_tensor.argtypes = [d, d, d, d, d, d, vp]
+        L.orc_demag_field.argtypes = [MP, vp, vp]
         _lib = L
     return _lib
 
@@ -362,8 +369,9 @@ class MsParams:
                  T_C=None, Ms0=None, A0=None, K0=None, dt=1e-16, gamma=C_GAMMA, seed=1,
                  T_amb=0.0, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0,
                  B0=0.0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0, ramp_len=0.0,
-                 head_x0=0.0, head_v=0.0, profile=None):
+                 head_x0=0.0, head_v=0.0, profile=None, demag=False):
         self.ncx, self.ncy, self.ncz = int(ncx), int(ncy), int(ncz)
+        self.demag = bool(demag)
         # head profile: dict(wz=, dz=, Bx0=, wx=, dx=) or None for a uniform field
         self.profile = dict(profile) if profile else None
         self.cell, self.ratio, self.wx = float(cell), int(ratio), int(wx)
@@ -397,6 +405,7 @@ class MsParams:
         s.Ms0, s.A0, s.K0 = self.Ms0, self.A0, self.K0
         s.lambda_, s.T_C = self.lam, self.T_C
         s.drv = self.drv.struct()
+        s.demag = int(self.demag)
         if self.profile:
             s.profile = 1
             s.prof_wz, s.prof_dz = self.profile["wz"], self.profile["dz"]
@@ -416,6 +425,22 @@ def ms_field(p, x, t):
     B = np.zeros(3)
     lib().orc_ms_field(ctypes.byref(s), float(x), float(t), _dp(B))
     return B
+
+
+def demag_tensor(X, Y, Z, dx, dy, dz):
+    """(Nxx, Nyy, Nzz, Nxy, Nxz, Nyz) between cuboid cells at offset (X, Y, Z) (Eq. 7)."""
+    N = np.zeros(6)
+    lib().orc_demag_tensor(float(X), float(Y), float(Z), float(dx), float(dy), float(dz), _dp(N))
+    return N
+
+
+def demag_field(p, M):
+    """B_d = -mu0 N * M on every cell of the track of p, by direct summation (M: (n_cells, 3) A/m)."""
+    s = p.struct()
+    M = np.ascontiguousarray(M, dtype=np.float64).reshape(-1)
+    Bd = np.zeros((p.n_cells, 3))
+    lib().orc_demag_field(ctypes.byref(s), _dp(M), _dp(Bd))
+    return Bd
 
 
 def ms_target(p, t):

@@ -15,7 +15,8 @@
  *
  * One coupled step n -> n+1 (t_n = n dt).  Drivers (laser temperature, write field) are
  * frozen at t_n for the whole step; the write field is uniform or follows the head with tanh
- * profiles along the track (orc_ms_field).
+ * profiles along the track (orc_ms_field).  Optionally the demagnetising field of Eq. 7
+ * (demag_stage, after stage 1) is added to the field of both regions, frozen for the step.
  *   1. Eq. 6: each cell inside the window takes the direction of the sum of its
  *      atomistic spins (0 for a non-magnetic cell).  The micromagnetic exchange of the
  *      neighbouring cells then sees the average atomistic direction (Sec. II).
@@ -57,6 +58,7 @@ typedef struct {
     double prof_wz, prof_dz; /* width and offset from the head of the profile of B0 dir [m] */
     double prof_Bx0;        /* amplitude of the in-plane (x) component [T] */
     double prof_wx, prof_dx; /* its width and offset from the head [m] */
+    int32_t demag;          /* 1: add the demagnetising field of Eq. 7 in both regions */
 } orc_ms_params;
 
 typedef struct {
@@ -70,6 +72,7 @@ typedef struct {
     double *S;              /* [3 nw] AoS, site (i, j, k) at i + nxw (j + nyw k) */
     int64_t step;           /* completed steps */
     int64_t events;         /* thermalisation events so far (window placements and moves) */
+    double *Bd;             /* [3 nc] demagnetising field of the current step [T], or NULL */
 } orc_ms;
 
 /* ------------------------------------------------------------------------- */
@@ -179,7 +182,7 @@ int64_t orc_ms_window_sites(const orc_ms_params *p)
 void orc_ms_destroy(orc_ms *c)
 {
     if (!c) return;
-    free(c->bits); free(c->grain); free(c->m); free(c->S);
+    free(c->bits); free(c->grain); free(c->m); free(c->S); free(c->Bd);
     free(c);
 }
 
@@ -199,6 +202,7 @@ orc_ms *orc_ms_create(const orc_ms_params *p, const int32_t *cell_grain)
     c->m = (double *)calloc(3 * (size_t)c->nc, sizeof(double));
     c->nw = orc_ms_window_sites(p);
     c->S = (double *)calloc(3 * (size_t)c->nw, sizeof(double));
+    c->Bd = (double *)calloc(3 * (size_t)c->nc, sizeof(double));
     return c;
 }
 
@@ -374,9 +378,10 @@ static int atom_step(orc_ms *c)
         orc_ms_field(p, ((double)c->ox * r + i + 0.5) * a, t, Bapp);
         site_exchange(c, c->S, i, j, k, g, ex);
         const double *Si = c->S + 3 * s;
-        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
-        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1];
-        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2];
+        const double *bd = c->Bd + 3 * site_cell(c, i, j, k);
+        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s] + bd[0];
+        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1] + bd[1];
+        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2] + bd[2];
         atom_rhs(c, Si, B, f1 + 3 * s);
         double v[3];
         for (int d = 0; d < 3; ++d) v[d] = Si[d] + dt * f1[3 * s + d];
@@ -393,9 +398,10 @@ static int atom_step(orc_ms *c)
         orc_ms_field(p, ((double)c->ox * r + i + 0.5) * a, t, Bapp);
         site_exchange(c, Sp, i, j, k, g, ex);
         const double *Spi = Sp + 3 * s;
-        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s];
-        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1];
-        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Spi[2] + Bapp[2] + Bth[3 * s + 2];
+        const double *bd = c->Bd + 3 * site_cell(c, i, j, k);
+        B[0] = ex[0] / p->mu_s + Bapp[0] + Bth[3 * s] + bd[0];
+        B[1] = ex[1] / p->mu_s + Bapp[1] + Bth[3 * s + 1] + bd[1];
+        B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Spi[2] + Bapp[2] + Bth[3 * s + 2] + bd[2];
         atom_rhs(c, Spi, B, f2);
         double *Si = c->S + 3 * s;
         double v[3];
@@ -428,7 +434,9 @@ static void mm_rate(const orc_ms *c, const double *V, int64_t q, double me, doub
     }
     double cex = 2.0 * p->A0 * me * me / (p->Ms0 * me), cK = 2.0 * p->K0 * me * me * me / (p->Ms0 * me);
     if (!(me > 0.0)) cex = cK = 0.0;
-    double B[3] = {cex * lap[0] + Bapp[0], cex * lap[1] + Bapp[1], cex * lap[2] + cK * mq[2] + Bapp[2]};
+    const double *bd = c->Bd + 3 * q;
+    double B[3] = {cex * lap[0] + Bapp[0] + bd[0], cex * lap[1] + Bapp[1] + bd[1],
+                   cex * lap[2] + cK * mq[2] + Bapp[2] + bd[2]};
     orc_params pp = p->drv;
     pp.alpha = orc_ms_alpha(p, T);
     orc_llg_rhs(&pp, mq, B, k);
@@ -482,6 +490,42 @@ static int mm_step(orc_ms *c)
     return 0;
 }
 
+void orc_demag_field(const orc_ms_params *p, const double *M, double *Bd);
+
+/* Stage 1b (with demag): the cells' magnetisation at t_n -- window cells
+ * M = (mu_s / V) sum_j m_j (Eq. 6), the others M = Ms0 m_e(T, |B_app|) m -- and
+ * B_d = -mu0 N * M (Eq. 7) on every cell, frozen for the step. */
+static int demag_stage(orc_ms *c)
+{
+    const orc_ms_params *p = &c->p;
+    const int r = p->ratio;
+    const int64_t nc = c->nc, nxw = (int64_t)p->wx * r, nyw = (int64_t)p->ncy * r;
+    const double t = (double)c->step * p->drv.dt, V = p->cell * p->cell * p->cell;
+    double *M = (double *)calloc(3 * (size_t)nc, sizeof(double));
+    if (!M) return -1;
+    for (int64_t q = 0; q < nc; ++q) {
+        if (c->grain[q] < 0) continue;
+        int64_t cx = q % p->ncx, cy = (q / p->ncx) % p->ncy, cz = q / ((int64_t)p->ncx * p->ncy);
+        if (cx >= c->ox && cx < c->ox + p->wx) {
+            for (int dk = 0; dk < r; ++dk)
+                for (int dj = 0; dj < r; ++dj)
+                    for (int di = 0; di < r; ++di) {
+                        int64_t i = (cx - c->ox) * r + di, j = cy * r + dj, k = cz * r + dk;
+                        const double *Si = c->S + 3 * (i + nxw * (j + nyw * k));
+                        for (int d = 0; d < 3; ++d) M[3 * q + d] += p->mu_s / V * Si[d];
+                    }
+        } else {
+            double B[3];
+            orc_ms_field(p, (cx + 0.5) * p->cell, t, B);
+            double me = orc_me(p->T_C, cell_temperature(c, q, t), p->mu_s, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+            for (int d = 0; d < 3; ++d) M[3 * q + d] = p->Ms0 * me * c->m[3 * q + d];
+        }
+    }
+    orc_demag_field(p, M, c->Bd);
+    free(M);
+    return 0;
+}
+
 /* The window's target column: centred on the laser spot at time t, within the track. */
 int32_t orc_ms_target(const orc_ms_params *p, double t)
 {
@@ -498,6 +542,7 @@ int orc_ms_run(orc_ms *c, int64_t n_steps, int32_t follow)
 {
     for (int64_t s = 0; s < n_steps; ++s) {
         average_cells(c, c->ox, c->ox + c->p.wx);
+        if (c->p.demag && demag_stage(c) != 0) return -1;
         if (atom_step(c) != 0) return -1;
         if (mm_step(c) != 0) return -1;
         c->step += 1;
@@ -536,5 +581,122 @@ void orc_ms_read_track(const orc_ms *c, double x_start, double bit_len, int32_t 
                 }
         signal[b] = count > 0 ? sum / (double)count : 0.0;
         if (bits) bits[b] = signal[b] < 0.0 ? 1 : 0;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Demagnetising field (Eq. 7): H = -N * M, a convolution of the cells' magnetisation with
+ * the demagnetising tensor of uniformly magnetised cuboid cells (Newell, Williams and
+ * Dunlop, J. Geophys. Res. 98, 9551 (1993)).  The tensor between two cells at offset
+ * (X, Y, Z) is the second difference over the cell edges of the functions f (diagonal) and
+ * g (off-diagonal) below, divided by 4 pi dx dy dz; beyond ORC_DIPOLE_CELLS cell edges it is
+ * the point-dipole tensor -(V / 4 pi r^3)(3 r r / r^2 - I), where the second difference
+ * cancels to rounding.  Atomistic moments enter through Eq. 6, M = (mu_s / V) sum_j m_j;
+ * micromagnetic cells carry M = Ms0 m_e(T) m. */
+#define ORC_DIPOLE_CELLS 40.0
+
+static double asinh_ratio(double a, double b)   /* asinh(a / b), 0 when b = 0 */
+{
+    return b > 0.0 ? asinh(a / b) : 0.0;
+}
+
+static double atan_ratio(double a, double b)    /* atan(a / b), 0 when b = 0 */
+{
+    return b != 0.0 ? atan(a / b) : 0.0;
+}
+
+double orc_newell_f(double x, double y, double z)
+{
+    x = fabs(x); y = fabs(y); z = fabs(z);
+    double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    double r = 0.0;
+    r += 0.5 * y * (z2 - x2) * asinh_ratio(y, sqrt(x2 + z2));
+    r += 0.5 * z * (y2 - x2) * asinh_ratio(z, sqrt(x2 + y2));
+    r -= x * y * z * atan_ratio(y * z, x * R);
+    r += (2.0 * x2 - y2 - z2) * R / 6.0;
+    return r;
+}
+
+double orc_newell_g(double x, double y, double z)
+{
+    double sx = x < 0 ? -1.0 : 1.0, sy = y < 0 ? -1.0 : 1.0;   /* g is odd in x and y, even in z */
+    x = fabs(x); y = fabs(y); z = fabs(z);
+    double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    double r = 0.0;
+    r += x * y * z * asinh_ratio(z, sqrt(x2 + y2));
+    r += y * (3.0 * z2 - y2) * asinh_ratio(x, sqrt(y2 + z2)) / 6.0;
+    r += x * (3.0 * z2 - x2) * asinh_ratio(y, sqrt(x2 + z2)) / 6.0;
+    r -= z2 * z * atan_ratio(x * y, z * R) / 6.0;
+    r -= 0.5 * z * y2 * atan_ratio(x * z, y * R);
+    r -= 0.5 * z * x2 * atan_ratio(y * z, x * R);
+    r -= x * y * R / 3.0;
+    return sx * sy * r;
+}
+
+/* second difference sum_{i,j,k} c_i c_j c_k F(X + i dx, Y + j dy, Z + k dz), c_0 = 2, c_+-1 = -1 */
+static double second_difference(double (*F)(double, double, double), double X, double Y, double Z, double dx,
+                                double dy, double dz)
+{
+    static const double c[3] = {-1.0, 2.0, -1.0};
+    double s = 0.0;
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j)
+            for (int k = -1; k <= 1; ++k)
+                s += c[i + 1] * c[j + 1] * c[k + 1] * F(X + i * dx, Y + j * dy, Z + k * dz);
+    return s;
+}
+
+static double f_yxz(double x, double y, double z) { return orc_newell_f(y, x, z); }
+static double f_zyx(double x, double y, double z) { return orc_newell_f(z, y, x); }
+static double g_xzy(double x, double y, double z) { return orc_newell_g(x, z, y); }
+static double g_yzx(double x, double y, double z) { return orc_newell_g(y, z, x); }
+
+/* The six components (xx, yy, zz, xy, xz, yz) of the tensor between cells at offset (X, Y, Z)
+ * for cells of edges (dx, dy, dz). */
+void orc_demag_tensor(double X, double Y, double Z, double dx, double dy, double dz, double N[6])
+{
+    double r = sqrt(X * X + Y * Y + Z * Z);
+    double lmax = fmax(dx, fmax(dy, dz));
+    if (r > ORC_DIPOLE_CELLS * lmax) {
+        double V = dx * dy * dz, pre = -V / (4.0 * ORC_PI * r * r * r), r2 = r * r;
+        N[0] = pre * (3.0 * X * X / r2 - 1.0);
+        N[1] = pre * (3.0 * Y * Y / r2 - 1.0);
+        N[2] = pre * (3.0 * Z * Z / r2 - 1.0);
+        N[3] = pre * 3.0 * X * Y / r2;
+        N[4] = pre * 3.0 * X * Z / r2;
+        N[5] = pre * 3.0 * Y * Z / r2;
+        return;
+    }
+    double k = 1.0 / (4.0 * ORC_PI * dx * dy * dz);
+    N[0] = k * second_difference(orc_newell_f, X, Y, Z, dx, dy, dz);
+    N[1] = k * second_difference(f_yxz, X, Y, Z, dx, dy, dz);
+    N[2] = k * second_difference(f_zyx, X, Y, Z, dx, dy, dz);
+    N[3] = k * second_difference(orc_newell_g, X, Y, Z, dx, dy, dz);
+    N[4] = k * second_difference(g_xzy, X, Y, Z, dx, dy, dz);
+    N[5] = k * second_difference(g_yzx, X, Y, Z, dx, dy, dz);
+}
+
+/* B_d = mu0 H_d = -mu0 sum_j N(r_i - r_j) M_j [T] on every cell, by direct summation, for the
+ * cell magnetisations M [A/m] (AoS 3 nc). */
+void orc_demag_field(const orc_ms_params *p, const double *M, double *Bd)
+{
+    const double mu0 = 1.25663706212e-6;
+    const int64_t nc = (int64_t)p->ncx * p->ncy * p->ncz;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < nc; ++i) {
+        int64_t ix = i % p->ncx, iy = (i / p->ncx) % p->ncy, iz = i / ((int64_t)p->ncx * p->ncy);
+        double h[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < nc; ++j) {
+            const double *Mj = M + 3 * j;
+            if (Mj[0] == 0.0 && Mj[1] == 0.0 && Mj[2] == 0.0) continue;
+            int64_t jx = j % p->ncx, jy = (j / p->ncx) % p->ncy, jz = j / ((int64_t)p->ncx * p->ncy);
+            double N[6];
+            orc_demag_tensor((ix - jx) * p->cell, (iy - jy) * p->cell, (iz - jz) * p->cell, p->cell, p->cell, p->cell,
+                             N);
+            h[0] += N[0] * Mj[0] + N[3] * Mj[1] + N[4] * Mj[2];
+            h[1] += N[3] * Mj[0] + N[1] * Mj[1] + N[5] * Mj[2];
+            h[2] += N[4] * Mj[0] + N[5] * Mj[1] + N[2] * Mj[2];
+        }
+        for (int d = 0; d < 3; ++d) Bd[3 * i + d] = -mu0 * h[d];
     }
 }

@@ -406,6 +406,104 @@ def check_isolated_cell_and_site_in_head_profile():
         assert np.linalg.norm(got - want) < 1e-8, (x, got, want)
 
 
+MU0 = 1.25663706212e-6
+
+
+def check_demag_tensor_limits():
+    """Demagnetising tensor of cuboid cells (Eq. 7, Newell et al. 1993): the self-term of a
+    cube is 1/3 on each axis with no off-diagonal part; every self-term has trace 1; a flat
+    cell tends to N_zz = 1 and a needle to N_zz = 0, N_xx = 1/2; the tensor is even in the
+    offset, N_xy odd in X; far away it is the point-dipole tensor -(V/4 pi r^3)(3 rr/r^2 - I)."""
+    a = 1e-9
+    N = o.demag_tensor(0, 0, 0, a, a, a)
+    assert np.allclose(N[:3], 1 / 3, atol=1e-14) and np.allclose(N[3:], 0, atol=1e-14)
+    for d in ((a, 2 * a, 0.5 * a), (3 * a, a, a), (a, a, 7 * a)):
+        assert abs(o.demag_tensor(0, 0, 0, *d)[:3].sum() - 1) < 1e-12
+    assert o.demag_tensor(0, 0, 0, 30 * a, 30 * a, 0.1 * a)[2] > 0.98
+    nd = o.demag_tensor(0, 0, 0, 0.05 * a, 0.05 * a, 20 * a)
+    assert nd[2] < 0.01 and abs(nd[0] - 0.5) < 0.01
+    r = np.array([2.3, -1.1, 0.7]) * a
+    assert np.allclose(o.demag_tensor(*r, a, a, a), o.demag_tensor(*(-r), a, a, a), rtol=1e-12, atol=0)
+    Nm = o.demag_tensor(-r[0], r[1], r[2], a, a, a)
+    assert abs(Nm[3] + o.demag_tensor(*r, a, a, a)[3]) < 1e-14
+    for k in (12.0, 30.0, 60.0):
+        X, Y, Z = k * a * 0.48, k * a * 0.6, k * a * 0.64
+        R = math.sqrt(X * X + Y * Y + Z * Z)
+        pre = -a ** 3 / (4 * math.pi * R ** 3)
+        want = [pre * (3 * X * X / R ** 2 - 1), pre * (3 * Y * Y / R ** 2 - 1), pre * (3 * Z * Z / R ** 2 - 1),
+                pre * 3 * X * Y / R ** 2, pre * 3 * X * Z / R ** 2, pre * 3 * Y * Z / R ** 2]
+        assert np.allclose(o.demag_tensor(X, Y, Z, a, a, a), want, rtol=2e-3 if k == 12.0 else 3e-4, atol=0)
+    # on either side of the cutoff of 40 cell edges the tensor is the dipole tensor at that point
+    for X, rtol in ((39.99 * a, 1e-4), (40.01 * a, 1e-12)):
+        want = -a ** 3 / (4 * math.pi * X ** 3) * np.array([2.0, -1.0, -1.0])
+        assert np.allclose(o.demag_tensor(X, 0, 0, a, a, a)[:3], want, rtol=rtol, atol=0)
+
+
+def check_demag_uniform_film():
+    """A uniformly magnetised film of 40 x 40 x 1 cells: at its centre the field is close to
+    -mu0 M for M normal to the film and close to 0 for M in its plane (the thin-film limits of
+    Eq. 7)."""
+    p = o.MsParams(40, 40, 1, 1e-9, 1, 1, J=J_SC)
+    Ms = 1e6
+    for Mdir, want in (((0, 0, 1), (0, 0, -MU0 * Ms)), ((1, 0, 0), (0, 0, 0))):
+        M = np.tile(np.array(Mdir, float) * Ms, (p.n_cells, 1))
+        Bd = o.demag_field(p, M)
+        c = 20 + 40 * 20
+        assert np.linalg.norm(Bd[c] - want) < 0.06 * MU0 * Ms, (Mdir, Bd[c])
+
+
+def check_demag_in_coupled_step():
+    """With the demagnetising field on and every other field off (J = 0, no anisotropy, no
+    applied field, T = 0, no damping), one short step turns each cell and window site by
+    -gamma m x B_d dt, with B_d = -mu0 N * M from the magnetisation assembled here: window cells
+    M = (mu_s / V) sum of their spins (Eq. 6), the other cells Ms0 m (m_e = 1 at T = 0)."""
+    dt = 1e-19
+    p = o.MsParams(6, 3, 2, 1e-9, 2, 2, J=0.0, ku=0.0, lam=0.0, dt=dt, T_amb=0.0, B0=0.0, seed=3, demag=True,
+                   Ms0=1.2e6, T_C=700.0)
+    grain = np.zeros(p.n_cells, np.int32)
+    grain[5] = -1
+    O = o.MsOracle(p, grain)
+    m0 = _tilted(p.n_cells, 8, 70.0)
+    m0[grain < 0] = 0.0
+    O.set_cells(m0)
+    O.set_window(2)
+    S0 = _tilted(O.nw, 9, 70.0)
+    nxw, nyw, nzw = p.window_dims
+    cell_of = lambda i, j, k: (2 + i // 2) + 6 * (j // 2 + 3 * (k // 2))
+    for k in range(nzw):
+        for j in range(nyw):
+            for i in range(nxw):
+                if grain[cell_of(i, j, k)] < 0:
+                    S0[i + nxw * (j + nyw * k)] = 0.0
+    O.set_moments(S0)
+    M = p.Ms0 * m0.copy()
+    V = 1e-27
+    for q in range(p.n_cells):
+        if 2 <= q % 6 < 4:
+            M[q] = 0.0
+    for k in range(nzw):
+        for j in range(nyw):
+            for i in range(nxw):
+                M[cell_of(i, j, k)] += p.mu_s / V * S0[i + nxw * (j + nyw * k)]
+    Bd = o.demag_field(p, M)
+    O.run(1)
+    dm = O.cells() - m0
+    for q in range(p.n_cells):
+        if grain[q] < 0 or 2 <= q % 6 < 4:
+            continue
+        want = -G * np.cross(m0[q], Bd[q]) * dt
+        assert np.linalg.norm(dm[q] - want) < 1e-4 * np.linalg.norm(want) + 1e-16, q
+    dS = O.moments() - S0
+    for k in range(nzw):
+        for j in range(nyw):
+            for i in range(nxw):
+                s = i + nxw * (j + nyw * k)
+                if grain[cell_of(i, j, k)] < 0:
+                    continue
+                want = -G * np.cross(S0[s], Bd[cell_of(i, j, k)]) * dt
+                assert np.linalg.norm(dS[s] - want) < 1e-4 * np.linalg.norm(want) + 1e-16, s
+
+
 def check_window_target():
     """The window is centred on the laser spot and stays on the track."""
     p = o.MsParams(20, 1, 1, 1e-9, 4, 6, J=J_SC, x0=10.2e-9, vx=1.0)
@@ -422,5 +520,6 @@ FAST_CHECKS = [
     check_uniform_state_stationary_through_shifts, check_isolated_cell_llg, check_mm_standing_spin_wave,
     check_ratio_one_window_matches_atomistic_lattice, check_full_window_equals_atomistic_oracle,
     check_shift_moves_spins, check_window_target, check_read_track, check_head_profile_shape,
-    check_isolated_cell_and_site_in_head_profile,
+    check_isolated_cell_and_site_in_head_profile, check_demag_tensor_limits, check_demag_uniform_film,
+    check_demag_in_coupled_step,
 ]

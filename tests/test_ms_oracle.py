@@ -50,6 +50,17 @@ MUTANTS = [
      "orc_applied_field(&p->drv, t, Bapp);\n        site_exchange(c, c->S,"),
     ("cells ignore the head profile", "orc_ms_field(p, (q % p->ncx + 0.5) * p->cell, t, Bq + 3 * q);",
      "orc_applied_field(&p->drv, t, Bq + 3 * q);"),
+    ("Newell f term sign", "r -= x * y * z * atan_ratio(y * z, x * R);", "r += x * y * z * atan_ratio(y * z, x * R);"),
+    ("Newell g last term", "r -= x * y * R / 3.0;", "r -= x * y * R / 6.0;"),
+    ("second-difference weights", "static const double c[3] = {-1.0, 2.0, -1.0};",
+     "static const double c[3] = {1.0, -2.0, 1.0};"),
+    ("far-field dipole sign", "pre = -V / (4.0 * ORC_PI * r * r * r)", "pre = V / (4.0 * ORC_PI * r * r * r)"),
+    ("window cells enter as directions", "M[3 * q + d] += p->mu_s / V * Si[d];", "M[3 * q + d] += Si[d];"),
+    ("window misses the demagnetising field",
+     "B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2] + bd[2];",
+     "B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2];"),
+    ("cells miss the demagnetising field", "double B[3] = {cex * lap[0] + Bapp[0] + bd[0],",
+     "double B[3] = {cex * lap[0] + Bapp[0],"),
 ]
 
 
