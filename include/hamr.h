@@ -293,6 +293,8 @@ void hamr_destroy(hamr_t h);
  *      lambda (1 - T / 3 T_C) with T capped at T_C, and m_e(T) the root in [0, 1] of
  *      m = L(3 T_C m / T + mu_s |B_app| / kB T), L(x) = coth x - 1/x (Sec. II); T is the
  *      laser temperature at the cell centre; m is renormalised after the step.
+ * With hamr_ms_set_demag the demagnetising field of Eq. 7 is added to both regions; with
+ * hamr_ms_set_head_profile the write field varies along the track.
  * Moving the window one column forward (hamr_ms_steps with follow): the trailing column
  * is handed to the micromagnetic side by Eq. 6, the sites shift back by one cell column
  * and the new leading column is thermalised: each site gets a spin whose polar angle from
@@ -344,6 +346,15 @@ int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], cons
  * m_e(T) law.  wz <= 0 restores the spatially uniform field B0 s(t) dir.  ARG on non-finite
  * values or wx <= 0. */
 int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, double wx, double dx);
+/* Demagnetising and stray field (Eq. 7) in both regions: B_d = -mu0 N * M on every cell,
+ * with N the demagnetising tensor of cubic cells (Newell, Williams and Dunlop, J. Geophys.
+ * Res. 98, 9551 (1993); the point-dipole tensor beyond 40 cell edges), M = Ms0 m_e(T) m on
+ * micromagnetic cells and M = (mu_s / V) sum of its spins on window cells (Eq. 6, Sec. II),
+ * recomputed every step from the state at t_n and added to the field of every cell and of
+ * every site in it.  Convolution by FFT on a zero-padded grid (cuFFT); the first call with
+ * on != 0 builds the tensor (host, FP64) and its transform.  on = 0 switches it off.
+ * Errors: OOM, CUDA. */
+int hamr_ms_set_demag(hamr_ms_t h, int32_t on);
 /* Micromagnetic directions m (3 ncx ncy ncz doubles, AoS; copied; non-magnetic cells are
  * set to 0).  ARG on non-finite values. */
 int hamr_ms_set_cells(hamr_ms_t h, const double *m);

@@ -69,7 +69,7 @@ def build(force=False, verbose=False, extra=()):
     objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp])
+        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-lcufft", "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 

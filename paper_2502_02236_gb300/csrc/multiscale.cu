@@ -21,8 +21,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cufft.h>
+
+#include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -212,11 +217,12 @@ __device__ __forceinline__ V3<Real> exchange(const MsDev &P, const Real *V, cons
 
 template <typename Real, int RT>
 __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const Real *m, const int *grain, MsDev P,
-                             ReplicaDev D, Field<Real> F, int ox, long long step) {
+                             ReplicaDev D, Field<Real> F, const Real *Bd, int ox, long long step) {
     int i, j, k;
     if (!coords(P.nxw, P.nyw, i, j, k)) return;
     const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
-    const int g = grain[cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k))];
+    const int qs = cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k));
+    const int g = grain[qs];
     if (g < 0) {
         Sp[s] = Sp[P.nw + s] = Sp[2 * P.nw + s] = Real(0);
         return;
@@ -232,7 +238,12 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
     BTH[s] = bthx;
     BTH[P.nw + s] = bthy;
     BTH[2 * P.nw + s] = bthz;
-    const V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * a);
+    V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * a);
+    if (Bd) {   // the demagnetising field of the site's cell (Eq. 7)
+        ba.x += Bd[qs];
+        ba.y += Bd[P.nc + qs];
+        ba.z += Bd[2 * P.nc + qs];
+    }
     const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g);
     const Real sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
     const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, ex.x / mu + ba.x + bthx,
@@ -250,14 +261,20 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
 
 template <typename Real, int RT>
 __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real *BTH, const Real *m, const int *grain,
-                             MsDev P, Field<Real> F, int ox, long long step) {
+                             MsDev P, Field<Real> F, const Real *Bd, int ox, long long step) {
     int i, j, k;
     if (!coords(P.nxw, P.nyw, i, j, k)) return;
     const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
-    const int g = grain[cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k))];
+    const int qs = cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k));
+    const int g = grain[qs];
     if (g < 0) return;
     const Real mu = (Real)P.mu_s, dt = (Real)P.dt;
-    const V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * (Real)P.a);
+    V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * (Real)P.a);
+    if (Bd) {
+        ba.x += Bd[qs];
+        ba.y += Bd[P.nc + qs];
+        ba.z += Bd[2 * P.nc + qs];
+    }
     const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g);
     const Real px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
     const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, ex.x / mu + ba.x + BTH[s],
@@ -304,7 +321,7 @@ __global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, 
 // stage buffers.
 template <typename Real>
 __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Field<Real> F, Real c, Real w, int first) {
+                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
     const int q = cell_at(P, cx, cy, cz);
@@ -325,7 +342,12 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     }
     const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
     const V3<Real> ba = field_at(P, F, (Real)((cx + 0.5) * P.cell));
-    const Real bx = ba.x, by = ba.y, bz = ba.z;
+    Real bx = ba.x, by = ba.y, bz = ba.z;
+    if (Bd) {
+        bx += Bd[q];
+        by += Bd[P.nc + q];
+        bz += Bd[2 * P.nc + q];
+    }
     const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz + cK * vz + bz);
     const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
                a2 = first ? Real(0) : acc[2 * P.nc + q];
@@ -469,6 +491,85 @@ __global__ void k_ms_read_track(const Real *m, const int *grain, MsDev P, double
     if (threadIdx.x == 0) signal[b] = scnt[0] > 0 ? ssum[0] / (double)scnt[0] : 0.0;
 }
 
+// ---- demagnetising field (Eq. 7) by FFT convolution on a zero-padded grid Px x Py x Pz
+struct Pad {
+    int Px, Py, Pz;
+    long long Ptot, Pc;   // real points, complex points (Px / 2 + 1 along x)
+};
+
+// The cells' magnetisation in the padded layout: window cells M = (mu_s / V) sum of their
+// spins (Eq. 6), other magnetic cells M = Ms0 m_e m, non-magnetic cells 0.
+template <typename Real>
+__global__ void k_demag_M(Real *Mpad, const Real *S, const Real *m, const double *me, const int *grain, MsDev P,
+                          Pad pd, int ox) {
+    int cx, cy, cz;
+    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    const int q = cell_at(P, cx, cy, cz);
+    const long long pp = cx + (long long)pd.Px * (cy + (long long)pd.Py * cz);
+    Real Mx = 0, My = 0, Mz = 0;
+    if (grain[q] >= 0) {
+        if (cx >= ox && cx < ox + P.wx) {
+            const Real scale = (Real)(P.mu_s / (P.cell * P.cell * P.cell));
+            for (int dk = 0; dk < P.r; ++dk)
+                for (int dj = 0; dj < P.r; ++dj)
+                    for (int di = 0; di < P.r; ++di) {
+                        const long long i = (long long)(cx - ox) * P.r + di, j = (long long)cy * P.r + dj,
+                                        k = (long long)cz * P.r + dk;
+                        const long long s = i + P.nxw * (j + (long long)P.nyw * k);
+                        Mx += scale * S[s];
+                        My += scale * S[P.nw + s];
+                        Mz += scale * S[2 * P.nw + s];
+                    }
+        } else {
+            const Real a = (Real)(P.Ms0 * me[q]);
+            Mx = a * m[q];
+            My = a * m[P.nc + q];
+            Mz = a * m[2 * P.nc + q];
+        }
+    }
+    Mpad[pp] = Mx;
+    Mpad[pd.Ptot + pp] = My;
+    Mpad[2 * pd.Ptot + pp] = Mz;
+}
+
+// H^ = N^ M^ at every frequency (N symmetric: xx, yy, zz, xy, xz, yz)
+template <typename C>
+__global__ void k_demag_multiply(C *Mh, const C *Nh, long long Pc) {
+    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (f >= Pc) return;
+    const C mx = Mh[f], my = Mh[Pc + f], mz = Mh[2 * Pc + f];
+    const C nxx = Nh[f], nyy = Nh[Pc + f], nzz = Nh[2 * Pc + f], nxy = Nh[3 * Pc + f], nxz = Nh[4 * Pc + f],
+            nyz = Nh[5 * Pc + f];
+    auto mul = [](C a, C b) {
+        C r;
+        r.x = a.x * b.x - a.y * b.y;
+        r.y = a.x * b.y + a.y * b.x;
+        return r;
+    };
+    auto add3 = [](C a, C b, C c) {
+        C r;
+        r.x = a.x + b.x + c.x;
+        r.y = a.y + b.y + c.y;
+        return r;
+    };
+    Mh[f] = add3(mul(nxx, mx), mul(nxy, my), mul(nxz, mz));
+    Mh[Pc + f] = add3(mul(nxy, mx), mul(nyy, my), mul(nyz, mz));
+    Mh[2 * Pc + f] = add3(mul(nxz, mx), mul(nyz, my), mul(nzz, mz));
+}
+
+// B_d = -mu0 H on every cell (the inverse transform is unnormalised: divide by Ptot)
+template <typename Real>
+__global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd) {
+    int cx, cy, cz;
+    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    const int q = cell_at(P, cx, cy, cz);
+    const long long pp = cx + (long long)pd.Px * (cy + (long long)pd.Py * cz);
+    const Real s = (Real)(-1.25663706212e-6 / (double)pd.Ptot);
+    Bd[q] = s * Hpad[pp];
+    Bd[P.nc + q] = s * Hpad[pd.Ptot + pp];
+    Bd[2 * P.nc + q] = s * Hpad[2 * pd.Ptot + pp];
+}
+
 constexpr int BLK = 256;
 inline unsigned nblk(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 inline dim3 grid3(int nx, int ny, int nz) { return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 3) / 4), (unsigned)nz); }
@@ -499,6 +600,12 @@ struct hamr_ms_ctx {
     long long step = 0;
     long long events = 0;         // thermalisation events so far
     bool grains_set = false, cells_set = false;
+    // demagnetising field (Eq. 7): padded grid, tensor spectra [6][Pc], work arrays, plans
+    bool demag = false;
+    Pad pad{};
+    void *Nh = nullptr, *Mpad = nullptr, *Mh = nullptr, *Bd = nullptr;
+    cufftHandle plan_f = 0, plan_b = 0;
+    bool plans = false;
 };
 
 namespace {
@@ -545,6 +652,17 @@ void ms_free(hamr_ms_t h) {
             cudaFree(*b);
             *b = nullptr;
         }
+    void **dbufs[] = {&h->Nh, &h->Mpad, &h->Mh, &h->Bd};
+    for (void **b : dbufs)
+        if (*b) {
+            cudaFree(*b);
+            *b = nullptr;
+        }
+    if (h->plans) {
+        cufftDestroy(h->plan_f);
+        cufftDestroy(h->plan_b);
+        h->plans = false;
+    }
     if (h->me) cudaFree(h->me);
     if (h->Tq) cudaFree(h->Tq);
     if (h->stage) cudaFree(h->stage);
@@ -620,6 +738,162 @@ Field<Real> field_of(const hamr_ms_t h, double t) {
     return F;
 }
 
+// ---- demagnetising tensor of cuboid cells (Newell, Williams and Dunlop, J. Geophys. Res. 98,
+// 9551 (1993)): the second difference over the cell edges of f (diagonal) and g (off-diagonal)
+// divided by 4 pi dx dy dz; beyond 40 cell edges the point-dipole tensor
+// -(V / 4 pi r^3)(3 r r / r^2 - I), where the second difference cancels to rounding.
+double nw_asinh(double a, double b) { return b > 0.0 ? asinh(a / b) : 0.0; }
+double nw_atan(double a, double b) { return b != 0.0 ? atan(a / b) : 0.0; }
+
+double newell_f(double x, double y, double z) {
+    x = fabs(x);
+    y = fabs(y);
+    z = fabs(z);
+    const double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    return 0.5 * y * (z2 - x2) * nw_asinh(y, sqrt(x2 + z2)) + 0.5 * z * (y2 - x2) * nw_asinh(z, sqrt(x2 + y2)) -
+           x * y * z * nw_atan(y * z, x * R) + (2.0 * x2 - y2 - z2) * R / 6.0;
+}
+
+double newell_g(double x, double y, double z) {
+    const double sg = (x < 0 ? -1.0 : 1.0) * (y < 0 ? -1.0 : 1.0);   // odd in x and y, even in z
+    x = fabs(x);
+    y = fabs(y);
+    z = fabs(z);
+    const double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    const double r = x * y * z * nw_asinh(z, sqrt(x2 + y2)) + y * (3.0 * z2 - y2) * nw_asinh(x, sqrt(y2 + z2)) / 6.0 +
+                     x * (3.0 * z2 - x2) * nw_asinh(y, sqrt(x2 + z2)) / 6.0 - z2 * z * nw_atan(x * y, z * R) / 6.0 -
+                     0.5 * z * y2 * nw_atan(x * z, y * R) - 0.5 * z * x2 * nw_atan(y * z, x * R) - x * y * R / 3.0;
+    return sg * r;
+}
+
+template <typename Fn>
+double second_diff(Fn F, double X, double Y, double Z, double d) {
+    const double c[3] = {-1.0, 2.0, -1.0};
+    double s = 0.0;
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j)
+            for (int k = -1; k <= 1; ++k) s += c[i + 1] * c[j + 1] * c[k + 1] * F(X + i * d, Y + j * d, Z + k * d);
+    return s;
+}
+
+// (xx, yy, zz, xy, xz, yz) between cubic cells of edge d at offset (X, Y, Z)
+void demag_tensor(double X, double Y, double Z, double d, double N[6]) {
+    const double r = sqrt(X * X + Y * Y + Z * Z);
+    if (r > 40.0 * d) {
+        const double pre = -d * d * d / (4.0 * M_PI * r * r * r), r2 = r * r;
+        N[0] = pre * (3.0 * X * X / r2 - 1.0);
+        N[1] = pre * (3.0 * Y * Y / r2 - 1.0);
+        N[2] = pre * (3.0 * Z * Z / r2 - 1.0);
+        N[3] = pre * 3.0 * X * Y / r2;
+        N[4] = pre * 3.0 * X * Z / r2;
+        N[5] = pre * 3.0 * Y * Z / r2;
+        return;
+    }
+    const double k = 1.0 / (4.0 * M_PI * d * d * d);
+    N[0] = k * second_diff([](double x, double y, double z) { return newell_f(x, y, z); }, X, Y, Z, d);
+    N[1] = k * second_diff([](double x, double y, double z) { return newell_f(y, x, z); }, X, Y, Z, d);
+    N[2] = k * second_diff([](double x, double y, double z) { return newell_f(z, y, x); }, X, Y, Z, d);
+    N[3] = k * second_diff([](double x, double y, double z) { return newell_g(x, y, z); }, X, Y, Z, d);
+    N[4] = k * second_diff([](double x, double y, double z) { return newell_g(x, z, y); }, X, Y, Z, d);
+    N[5] = k * second_diff([](double x, double y, double z) { return newell_g(y, z, x); }, X, Y, Z, d);
+}
+
+// offset of padded index i along an axis of n cells padded to P (INT32_MIN: not a cell offset)
+int pad_offset(int i, int n, int P) {
+    if (i < n) return i;
+    if (i > P - n) return i - P;
+    return INT32_MIN;
+}
+
+template <typename Real>
+int ms_demag_setup(hamr_ms_t h) {
+    typedef typename std::conditional<sizeof(Real) == 8, cufftDoubleComplex, cufftComplex>::type C;
+    const MsDev &P = h->P;
+    Pad &pd = h->pad;
+    pd.Px = P.ncx > 1 ? 2 * P.ncx : 1;
+    pd.Py = P.ncy > 1 ? 2 * P.ncy : 1;
+    pd.Pz = P.ncz > 1 ? 2 * P.ncz : 1;
+    pd.Ptot = (long long)pd.Px * pd.Py * pd.Pz;
+    pd.Pc = (long long)(pd.Px / 2 + 1) * pd.Py * pd.Pz;
+    // tensor on the padded grid, on the host, in parallel over z planes
+    std::vector<double> T(6 * (size_t)pd.Ptot, 0.0);
+    const unsigned nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < nth; ++w)
+        pool.emplace_back([&, w]() {
+            for (int k = (int)w; k < pd.Pz; k += (int)nth) {
+                const int Z = pad_offset(k, P.ncz, pd.Pz);
+                if (Z == INT32_MIN) continue;
+                for (int j = 0; j < pd.Py; ++j) {
+                    const int Y = pad_offset(j, P.ncy, pd.Py);
+                    if (Y == INT32_MIN) continue;
+                    for (int i = 0; i < pd.Px; ++i) {
+                        const int X = pad_offset(i, P.ncx, pd.Px);
+                        if (X == INT32_MIN) continue;
+                        double N[6];
+                        demag_tensor(X * P.cell, Y * P.cell, Z * P.cell, P.cell, N);
+                        const long long pp = i + (long long)pd.Px * (j + (long long)pd.Py * k);
+                        for (int c = 0; c < 6; ++c) T[(size_t)c * pd.Ptot + pp] = N[c];
+                    }
+                }
+            }
+        });
+    for (auto &t : pool) t.join();
+    std::vector<Real> Tr(T.begin(), T.end());
+    MSCK(h, cudaMalloc(&h->Nh, sizeof(C) * 6 * pd.Pc));
+    MSCK(h, cudaMalloc(&h->Mh, sizeof(C) * 3 * pd.Pc));
+    // [M | H], each 3 padded grids; the tensor's six components pass through it once at setup
+    MSCK(h, cudaMalloc(&h->Mpad, sizeof(Real) * 6 * pd.Ptot));
+    MSCK(h, cudaMalloc(&h->Bd, sizeof(Real) * 3 * P.nc));
+    int n[3] = {pd.Pz, pd.Py, pd.Px};
+    const bool dbl = sizeof(Real) == 8;
+    if (cufftPlanMany(&h->plan_f, 3, n, nullptr, 1, (int)pd.Ptot, nullptr, 1, (int)pd.Pc, dbl ? CUFFT_D2Z : CUFFT_R2C,
+                      3) != CUFFT_SUCCESS ||
+        cufftPlanMany(&h->plan_b, 3, n, nullptr, 1, (int)pd.Pc, nullptr, 1, (int)pd.Ptot, dbl ? CUFFT_Z2D : CUFFT_C2R,
+                      3) != CUFFT_SUCCESS)
+        return msfail(h, HAMR_ERR_CUDA, "cuFFT plan creation failed for a %d x %d x %d grid", pd.Px, pd.Py, pd.Pz);
+    h->plans = true;
+    cufftSetStream(h->plan_f, h->stream);
+    cufftSetStream(h->plan_b, h->stream);
+    MSCK(h, cudaMemcpyAsync(h->Mpad, Tr.data(), sizeof(Real) * 6 * pd.Ptot, cudaMemcpyHostToDevice, h->stream));
+    for (int half = 0; half < 2; ++half) {
+        Real *src = (Real *)h->Mpad + (size_t)half * 3 * pd.Ptot;
+        C *dst = (C *)h->Nh + (size_t)half * 3 * pd.Pc;
+        const cufftResult r = dbl ? cufftExecD2Z(h->plan_f, (cufftDoubleReal *)src, (cufftDoubleComplex *)dst)
+                                  : cufftExecR2C(h->plan_f, (cufftReal *)src, (cufftComplex *)dst);
+        if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform of the tensor failed");
+    }
+    MSCK(h, cudaMemsetAsync(h->Mpad, 0, sizeof(Real) * 6 * pd.Ptot, h->stream));
+    MSCK(h, cudaStreamSynchronize(h->stream));
+    return HAMR_OK;
+}
+
+// B_d = -mu0 N * M of the current state (the m_e of each cell must be current)
+template <typename Real>
+int ms_demag_step(hamr_ms_t h) {
+    typedef typename std::conditional<sizeof(Real) == 8, cufftDoubleComplex, cufftComplex>::type C;
+    const MsDev &P = h->P;
+    const Pad &pd = h->pad;
+    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
+    k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Mpad, (const Real *)h->S, (const Real *)h->m, h->me,
+                                                h->grain_d, P, pd, h->ox);
+    MSCK(h, cudaGetLastError());
+    const bool dbl = sizeof(Real) == 8;
+    cufftResult r = dbl ? cufftExecD2Z(h->plan_f, (cufftDoubleReal *)h->Mpad, (cufftDoubleComplex *)h->Mh)
+                        : cufftExecR2C(h->plan_f, (cufftReal *)h->Mpad, (cufftComplex *)h->Mh);
+    if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform failed");
+    k_demag_multiply<C><<<nblk(pd.Pc), BLK, 0, h->stream>>>((C *)h->Mh, (const C *)h->Nh, pd.Pc);
+    MSCK(h, cudaGetLastError());
+    // H goes to the second half of the buffer: the padding of M (first half) must stay zero
+    Real *H = (Real *)h->Mpad + 3 * pd.Ptot;
+    r = dbl ? cufftExecZ2D(h->plan_b, (cufftDoubleComplex *)h->Mh, (cufftDoubleReal *)H)
+            : cufftExecC2R(h->plan_b, (cufftComplex *)h->Mh, (cufftReal *)H);
+    if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT inverse transform failed");
+    k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Bd, H, P, pd);
+    MSCK(h, cudaGetLastError());
+    return HAMR_OK;
+}
+
 template <typename Real>
 int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
     const long long n = (long long)(cx1 - cx0) * h->P.r * h->P.nyw * h->P.nzw;
@@ -660,13 +934,25 @@ int ms_step(hamr_ms_t h) {
     int rc = ms_average<Real>(h, h->ox, P.wx);
     if (rc) return rc;
     Real *S = (Real *)h->S, *Sp = (Real *)h->Sp, *F1 = (Real *)h->F1, *BTH = (Real *)h->BTH, *m = (Real *)h->m;
-    const dim3 gw = grid3(P.nxw, P.nyw, P.nzw);
     const double t = (double)h->step * P.dt;
     const Field<Real> F = field_of<Real>(h, t);
-#define MS_HEUN(RT)                                                                                          \
-    do {                                                                                                     \
-        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, F, h->ox, h->step); \
-        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, F, h->ox, h->step);       \
+    // m_e(T) of every cell at t_n, then (optionally) the demagnetising field of the state at t_n
+    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
+    const double Bm = field_magnitude_host(h, t);
+    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, field_of<double>(h, t),
+                                         h->Bm_last);
+    h->Bm_last = Bm;
+    MSCK(h, cudaGetLastError());
+    const Real *Bd = nullptr;
+    if (h->demag) {
+        if ((rc = ms_demag_step<Real>(h))) return rc;
+        Bd = (const Real *)h->Bd;
+    }
+    const dim3 gw = grid3(P.nxw, P.nyw, P.nzw);
+#define MS_HEUN(RT)                                                                                              \
+    do {                                                                                                         \
+        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, F, Bd, h->ox, h->step); \
+        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, F, Bd, h->ox, h->step);       \
     } while (0)
     switch (P.r) {
         case 1: MS_HEUN(1); break;
@@ -676,11 +962,6 @@ int ms_step(hamr_ms_t h) {
     }
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
-    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
-    const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, field_of<double>(h, t),
-                                         h->Bm_last);
-    h->Bm_last = Bm;
     MSCK(h, cudaMemcpyAsync(h->V0, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
     MSCK(h, cudaMemcpyAsync(h->V1, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
     const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
@@ -688,7 +969,7 @@ int ms_step(hamr_ms_t h) {
         const Real *vin = (const Real *)((s & 1) ? h->V1 : h->V0);
         Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
         k_mm_stage<Real><<<gc, BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m, (const Real *)h->coef, h->grain_d, P, h->ox,
-                                              F, cst[s], wst[s], s == 0);
+                                              F, Bd, cst[s], wst[s], s == 0);
     }
     k_mm_final<Real><<<gc, BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox);
     MSCK(h, cudaGetLastError());
@@ -891,6 +1172,21 @@ int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, doub
     h->P.pdz = dz;
     h->P.pwx = wx;
     h->P.pdx = dx;
+    return HAMR_OK;
+}
+
+int hamr_ms_set_demag(hamr_ms_t h, int32_t on) {
+    if (!h) return HAMR_ERR_ARG;
+    if (!on) {
+        h->demag = false;
+        return HAMR_OK;
+    }
+    MsDeviceGuard dg(h->device);
+    if (!h->plans) {
+        const int rc = h->prec == HAMR_FP64 ? ms_demag_setup<double>(h) : ms_demag_setup<float>(h);
+        if (rc) return rc;
+    }
+    h->demag = true;
     return HAMR_OK;
 }
 

@@ -14,14 +14,14 @@ TOL = {"fp64": 1e-9, "fp32": 2e-4}
 PRECISIONS = ["fp64", "fp32"]
 
 
-def pair(w, precision="fp64", profile=None):
+def pair(w, precision="fp64", profile=None, demag=False):
     """The oracle and the GPU handle for one multiscale input description."""
     T, F = w["T"], w["field"]
     p = orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                      ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
                      seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
                      bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"],
-                     profile=profile)
+                     profile=profile, demag=demag)
     O = orc.MsOracle(p, w["grain"])
     G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                    ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
@@ -31,6 +31,8 @@ def pair(w, precision="fp64", profile=None):
     G.set_field_sequence(**F)
     if profile:
         G.set_head_profile(**profile)
+    if demag:
+        G.set_demag(True)
     return p, O, G
 
 
@@ -149,6 +151,25 @@ def test_head_profile_matches_oracle(prec):
         with pytest.raises(HamrError) as e:
             G.set_head_profile(Bx0=0.1, wz=1e-9, wx=0.0)
         assert e.value.code == ERR_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_demag_matches_oracle(prec):
+    """The demagnetising field of Eq. 7 (FFT convolution on the GPU, direct summation in the
+    oracle) in both regions, with the laser on and the window following the spot."""
+    w = I.multiscale_track(ncx=24, ncy=6, ncz=3, cell=1e-9, ratio=2, wx=6, grain_d=5e-9, seed=27, v=1.5e5,
+                           x_spot=9.013e-9)
+    p, O, G = pair(w, prec, demag=True)
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        ox = O.window
+        O.run(100, follow=True)
+        G.steps(100, follow=True)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], (dm, dS)
+        assert G.window()[0] == O.window >= ox + 1
+        G.set_demag(False)
 
 
 @pytest.mark.gpu
