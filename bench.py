@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-ms", action="store_true", help="skip the multiscale-track line")
     p.add_argument("--ms-steps", type=int, default=20)
+    p.add_argument("--ms-demag", action="store_true",
+                   help="with --workload multiscale_track: the demagnetising field on")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--tile", default=None, help="fused-kernel shape THREADSxSTAGED instead of autotuning")
     return p.parse_args()
@@ -303,7 +305,7 @@ def multiscale_line(args, dist):
     m[:, 2] = 1.0
     ox = int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5))
 
-    def rate(precision, K):
+    def rate(precision, K, demag=False):
         G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                        ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
                        seed=w["seed"] ^ (dist.rank << 48), precision=precision)
@@ -312,6 +314,8 @@ def multiscale_line(args, dist):
         G.set_field_sequence(**w["field"])
         G.set_cells(m)
         G.set_window(ox)
+        if demag:
+            G.set_demag(True)
         G.steps(3, follow=True)
         dist.barrier()
         torch.cuda.synchronize()
@@ -328,11 +332,14 @@ def multiscale_line(args, dist):
     K = max(1, args.ms_steps)
     t32, nw, nc = rate("fp32", 5 * K)
     t64, _, _ = rate("fp64", K)
+    t32d, _, _ = rate("fp32", K, demag=True)
     line = {"workload": "multiscale_track", "dtype": "f32", "window_sites": nw, "cells": nc, "steps": 5 * K,
             "ms_per_step": t32, "window_spin_steps_per_s": nw * dist.world / (t32 / 1e3),
             "cell_steps_per_s": nc * dist.world / (t32 / 1e3),
             "fp64": {"ms_per_step": t64, "window_spin_steps_per_s": nw * dist.world / (t64 / 1e3), "steps": K},
             "speedup_fp32_over_fp64": t64 / t32,
+            "fp32_with_demag": {"ms_per_step": t32d, "window_spin_steps_per_s": nw * dist.world / (t32d / 1e3),
+                                "steps": K, "note": "Eq. 7 by FFT convolution on the 1000 x 120 x 20 padded grid"},
             "launches_per_step": 10, "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot"}
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
         import oracle as orc
@@ -353,6 +360,48 @@ def multiscale_line(args, dist):
     return line
 
 
+def multiscale_only(args, dist):
+    """bench.py --workload multiscale_track: the multiscale track alone, FP32, K = --steps
+    coupled steps after --warmup (the demagnetising field on with --ms-demag); one JSON line."""
+    import torch
+    from paper_2502_02236_gb300 import inputs as I
+    from paper_2502_02236_gb300.hamr import Multiscale
+    w = I.multiscale_track()
+    G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"], ku=w["ku"],
+                   Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
+                   seed=w["seed"] ^ (dist.rank << 48), precision="fp32")
+    G.set_grain_map(w["grain"])
+    G.set_temperature_profile(**w["T"])
+    G.set_field_sequence(**w["field"])
+    m = np.zeros((G.n_cells, 3))
+    m[:, 2] = 1.0
+    G.set_cells(m)
+    G.set_window(int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5)))
+    if args.ms_demag:
+        G.set_demag(True)
+    G.steps(max(3, args.warmup), follow=True)
+    K = max(1, args.steps)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.steps(K, follow=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    nw = G.n_window
+    G.close()
+    out = {"metric": "window spin-steps/s (multiscale track, FP32)", "value": nw * K * dist.world / (ms / 1e3),
+           "unit": "spin-steps/s", "n_gpus": dist.world, "steps": K, "warmup": max(3, args.warmup),
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": "multiscale_track", "demag": bool(args.ms_demag),
+                                           "window_sites": nw, "cells": G.n_cells}}
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -368,6 +417,8 @@ def main():
     torch.cuda.set_device(dist.local)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)     # the library runs on (and is timed on) this stream
+    if args.workload == "multiscale_track":
+        return multiscale_only(args, dist)
     W = max(3, args.warmup)
     K = args.steps
     w = I.workload(args.workload)
