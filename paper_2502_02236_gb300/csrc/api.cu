@@ -229,6 +229,7 @@ int refresh_grains(hamr_t h) {
         G += h->n_grains[r];
     }
     h->G = G;
+    h->runs_dirty = true;
     h->gcount_h.assign(std::max(G, 1), 0);
     for (int r = 0; r < h->R; ++r)
         std::copy(h->gcount_rep[r].begin(), h->gcount_rep[r].end(), h->gcount_h.begin() + h->reps_h[r].grain_off);
@@ -253,6 +254,66 @@ int refresh_grains(hamr_t h) {
     h->grain_last_h.assign(3 * (size_t)std::max(G, 1), 0.0);
     CK(h, cudaMemcpyAsync(h->reps_d, h->reps_h.data(), sizeof(ReplicaDev) * h->R, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    return HAMR_OK;
+}
+
+// Runs of consecutive magnetic slots of one grain (within one row, at most GRAIN_RUN_MAX
+// long), grouped by global grain bin, and the items of up to GRAIN_RUN_MAX runs of one grain
+// that the per-grain sums of the FP32 fused path take one warp each.
+int build_runs(hamr_t h) {
+    Range nv("hamr build_runs");
+    std::vector<unsigned long long> run;
+    std::vector<int> run_grain;
+    std::vector<long long> per_grain(std::max(h->G, 1) + 1, 0);
+    for (int r = 0; r < h->R; ++r) {
+        const ReplicaDev &R = h->reps_h[r];
+        for (long long z = 0; z < R.nz; ++z)
+            for (long long y = 0; y < R.ny; ++y) {
+                const long long row = slot_of(R, 0, y, z);
+                long long x = 0;
+                while (x < R.nx) {
+                    const uint16_t g = h->gcode_h[row + x];
+                    long long e = x + 1;
+                    while (e < R.nx && e - x < GRAIN_RUN_MAX && h->gcode_h[row + e] == g) ++e;
+                    if (g) {
+                        run.push_back((unsigned long long)(row + x) << 5 | (unsigned long long)(e - x - 1));
+                        run_grain.push_back(R.grain_off + g - 1);
+                        per_grain[R.grain_off + g] += 1;
+                    }
+                    x = e;
+                }
+            }
+    }
+    for (size_t g = 1; g < per_grain.size(); ++g) per_grain[g] += per_grain[g - 1];
+    std::vector<unsigned long long> sorted(run.size());
+    std::vector<long long> fill(per_grain.begin(), per_grain.end() - 1);
+    for (size_t i = 0; i < run.size(); ++i) sorted[fill[run_grain[i]]++] = run[i];
+    std::vector<GrainRunItem> items;
+    for (int g = 0; g < h->G; ++g)
+        for (long long k = per_grain[g]; k < per_grain[g + 1]; k += GRAIN_RUN_MAX)
+            items.push_back({k, g, (int)std::min<long long>(GRAIN_RUN_MAX, per_grain[g + 1] - k)});
+    if ((long long)sorted.size() > h->runs_cap) {
+        dfree(h->runs_d);
+        const long long cap = std::max<long long>((long long)sorted.size(), 2 * h->runs_cap);
+        CK(h, dalloc(h, &h->runs_d, (size_t)cap));
+        h->runs_cap = cap;
+    }
+    if ((int)items.size() > h->gitems_cap) {
+        dfree(h->gitems_d);
+        const int cap = std::max((int)items.size(), 2 * h->gitems_cap);
+        CK(h, dalloc(h, &h->gitems_d, (size_t)cap));
+        h->gitems_cap = cap;
+    }
+    if (!sorted.empty())
+        CK(h, cudaMemcpyAsync(h->runs_d, sorted.data(), sizeof(unsigned long long) * sorted.size(),
+                              cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CK(h, cudaMemcpyAsync(h->gitems_d, items.data(), sizeof(GrainRunItem) * items.size(), cudaMemcpyHostToDevice,
+                              h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->n_gitems = (int)items.size();
+    h->runs_dirty = false;
+    clear_graphs(h);
     return HAMR_OK;
 }
 
@@ -517,7 +578,6 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.ay = (float)h->ph.ay;
         a.az = (float)h->ph.az;
         for (int d = 0; d < 3; ++d) a.per[d] = h->per[d];
-        a.grain_fx = h->grain_fx_d;
         a.maps = h->maps_d;
         a.wait_polls = h->inject_polls ? h->inject_polls : (1u << 22);
         a.inject = h->inject_polls ? 1 : 0;
@@ -525,8 +585,11 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.Sbuf1 = (float *)h->S[1];
         for (int i = 0; i < G; ++i) {
             a.step_off = i;
-            CK(h, launch_fused_step(h->variant, tetragonal(h), a, h->fused_grid, record && i == G - 1, h->stream));
+            CK(h, launch_fused_step(h->variant, tetragonal(h), a, h->fused_grid, h->stream));
         }
+        if (record)
+            CK(h, launch_grain_sums_fx(a.Sbuf0, a.Sbuf1, h->NS, h->runs_d, h->gitems_d, h->n_gitems, h->ctl_d, G,
+                                       h->grain_fx_d, h->stream));
     } else {
         const int nb = (int)(h->NS / PLAIN_BLOCK);
         if (h->prec == HAMR_FP64) {
@@ -658,6 +721,10 @@ int steps_impl(hamr_t h, int64_t n_steps, int32_t record_every, bool sync) {
         int rc = collect_records(h);
         if (rc) return rc;
     }
+    if (fused_mode(h) && nrec > 0 && h->runs_dirty) {
+        int rc = build_runs(h);
+        if (rc) return rc;
+    }
     if (nrec > h->rec_cap) {
         dfree(h->rec_d);
         dfree(h->rec_step_d);
@@ -716,6 +783,8 @@ void destroy_device(hamr_t h) {
     dfree(h->dscratch_d);
     dfree(h->stage_d);
     dfree(h->items_d);
+    dfree(h->runs_d);
+    dfree(h->gitems_d);
 }
 
 int init_device(hamr_t h, long long NS, long long maxn, const std::vector<int> &blk_rep) {

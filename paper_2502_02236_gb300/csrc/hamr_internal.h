@@ -65,6 +65,16 @@ struct Ctl {
 };
 
 // One unit of work of the fused kernel: a block of columns of one replica.
+// Runs of consecutive storage slots of one grain (at most GRAIN_RUN_MAX slots, within one
+// row), packed as slot << 5 | (length - 1) and grouped by global grain bin; an item is up
+// to GRAIN_RUN_MAX runs of one grain, summed by one warp.
+constexpr int GRAIN_RUN_MAX = 32;
+struct GrainRunItem {
+    long long run0;  // first run of the item
+    int grain;       // global grain bin
+    int n_runs;      // 1 .. GRAIN_RUN_MAX
+};
+
 struct WorkItem {
     int r;         // replica
     int x0, y0;    // first interior column
@@ -113,7 +123,6 @@ struct FusedArgs {
     float cJ[3];                // J_s / mu_s of the stencil's shells (SC: shell 0 only) [T]
     float cK, pref, alpha, dt, sig0, ax, ay, az;
     int per[3];
-    unsigned long long *grain_fx;  // [G][3] fixed-point (2^-24) sums at record steps
     const CUtensorMap *maps;       // [R][2] tensor maps of each replica's state in each buffer
     unsigned wait_polls;           // a bounded device wait fails after this many polls
     int inject;                    // failure-detection test: 1 = the CTA of work item 0 withholds
@@ -123,7 +132,12 @@ struct FusedArgs {
 // kernel launchers (kernels_*.cu)
 cudaError_t launch_plain_step(int prec, const void *args, int n_blocks, bool record, cudaStream_t st);
 // tet: the L1_0 (tetragonal three-shell) stencil instead of the simple-cubic one
-cudaError_t launch_fused_step(int variant, bool tet, const FusedArgs &a, int grid, bool record, cudaStream_t st);
+cudaError_t launch_fused_step(int variant, bool tet, const FusedArgs &a, int grid, cudaStream_t st);
+// exact per-grain sums (fixed point, 2^-24) of the FP32 state after G steps from ctl->step,
+// into grain_fx (read by k_bookkeeping at a record point)
+cudaError_t launch_grain_sums_fx(const float *S0, const float *S1, long long NS, const unsigned long long *runs,
+                                 const GrainRunItem *items, int n_items, const Ctl *ctl, int G,
+                                 unsigned long long *grain_fx, cudaStream_t st);
 bool fused_variant(int variant, FusedVariant &out);
 int fused_max_blocks_per_sm(int variant, bool tet);
 cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps,
@@ -214,6 +228,12 @@ struct hamr_ctx {
     int fused_grid = 0;
     unsigned inject_polls = 0;        // >0: the next step block runs the failure test
     bool items_dirty = true;
+    // per-grain runs for the record sums of the FP32 fused path (rebuilt after grain changes)
+    unsigned long long *runs_d = nullptr;
+    hamr::GrainRunItem *gitems_d = nullptr;
+    long long runs_cap = 0;
+    int gitems_cap = 0, n_gitems = 0;
+    bool runs_dirty = true;
     int num_sms = 0;
     size_t dev_bytes = 0;
 

@@ -37,8 +37,9 @@
 // Each site's thermal normals come from its own (replica key, site, step) Philox counter, so
 // halo sites computed by two CTAs get the same noise.  Open edges and non-magnetic sites read
 // as S = 0 (the state of such sites is kept at 0): a zero spin marks a non-magnetic site and
-// adds nothing to the exchange sum, so grain codes are read only at record steps (for the
-// per-grain sums) and for replicas whose grains touch (the exchange mask).
+// adds nothing to the exchange sum, so grain codes are read only for replicas whose grains
+// touch (the exchange mask).  The per-grain sums of record steps are taken afterwards by a
+// separate coalesced pass over the new state (k_grain_sums_fx).
 // Per step the kernel reads S once (12 B/site) and writes S once (12 B/site); halo columns
 // are re-read from L2.
 #pragma once
@@ -150,9 +151,8 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 
 // f(S, B) / (dt pref) = S x B + alpha [(S.B) S - (S.S) B]  (Eq. 1 in Landau-Lifshitz form).
 // The fused kernels are compiled without implicit multiply-add contraction, and every fused
-// multiply-add here is written out, so that all instantiations (with and without records,
-// every launch shape) round identically and a run resumed with different step blocks is
-// bitwise the same.
+// multiply-add here is written out, so that all instantiations (every launch shape) round
+// identically and a run resumed with different step blocks is bitwise the same.
 __device__ __forceinline__ float3 rhs_u(float sx, float sy, float sz, float ss, float bx, float by, float bz,
                                         float al) {
     const float cx = fmaf(sy, bz, -(sz * by)), cy = fmaf(sz, bx, -(sx * bz)), cz = fmaf(sx, by, -(sy * bx));
@@ -258,7 +258,7 @@ __device__ __forceinline__ float3 field_p(const FusedArgs &a, float3 h, const fl
                        fmaf(a.cJ[0], nn.z, fmaf(a.cJ[1], zz.z, fmaf(a.cJ[2], dg.z, h.z))));
 }
 
-template <bool TET, int NT, int E, int SW, int SH, int MINB, bool RECORD>
+template <bool TET, int NT, int E, int SW, int SH, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     using Sh = FusedShape<NT, SW, SH>;
     constexpr int CAPS = Sh::CAPS, LPT = Sh::LPT, SLOT_F = Sh::SLOT_F;
@@ -443,14 +443,11 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         unsigned gm1[E];               // grain code of plane k-1 (masked replicas)
         float amx[E], amy[E], amz[E];  // S + dt f(S, B(S)) / 2 of plane k-1
         float hmx[E], hmy[E], hmz[E];  // B_app + B_th of plane k-1
-        int ax_[E], ay_[E], az_[E], gacc[E];  // fixed-point record sums of each column
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             m1x[j] = m1y[j] = m1z[j] = c0x[j] = c0y[j] = c0z[j] = 0.f;
             amx[j] = amy[j] = amz[j] = hmx[j] = hmy[j] = hmz[j] = 0.f;
             gm1[j] = 0;
-            ax_[j] = ay_[j] = az_[j] = 0;
-            gacc[j] = -1;
             if (act[j]) {
                 const float *S2 = sS + 2 * SLOT_F + c[j], *S3 = sS + 3 * SLOT_F + c[j];  // planes -2, -1
                 m1x[j] = S2[0];
@@ -588,22 +585,6 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                     Sout[o] = ox;
                     Sout[NS + o] = oy;
                     Sout[2 * NS + o] = oz;
-                    if (RECORD) {
-                        const unsigned g = mask ? __float_as_uint(v.w) : (unsigned)__ldg(a.gcode + o);
-                        const int gg = R.grain_off + (int)g - 1;
-                        if (gg != gacc[j] || (kc & 63) == 63) {
-                            if (gacc[j] >= 0) {
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 0, (unsigned long long)(long long)ax_[j]);
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 1, (unsigned long long)(long long)ay_[j]);
-                                atomicAdd(a.grain_fx + 3 * gacc[j] + 2, (unsigned long long)(long long)az_[j]);
-                            }
-                            gacc[j] = gg;
-                            ax_[j] = ay_[j] = az_[j] = 0;
-                        }
-                        ax_[j] += __float2int_rn(ox * FX_SCALE);
-                        ay_[j] += __float2int_rn(oy * FX_SCALE);
-                        az_[j] += __float2int_rn(oz * FX_SCALE);
-                    }
                 }
             }
             // carry each column's plane-k values to the next march step
@@ -641,9 +622,6 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                     mbar_wait(&s_bar[slot], (s_ph >> slot) & 1, 1u << 22);
                     s_ph ^= 1 << slot;
                 }
-        } else if (RECORD) {
-#pragma unroll
-            for (int j = 0; j < E; ++j) grain_accumulate_fx(a.grain_fx, gacc[j], ax_[j], ay_[j], az_[j], gacc[j] >= 0);
         }
         }  // marching warps
         // all reads of this item's slots are done before they are re-armed; a failed wait ends
@@ -659,11 +637,8 @@ static cudaError_t ensure_attrs() {
     using Sh = FusedShape<NT, SW, SH>;
     static bool init = false;
     if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB, false>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Sh::smem);
         if (e != cudaSuccess) return e;
         init = true;
     }
@@ -671,14 +646,11 @@ static cudaError_t ensure_attrs() {
 }
 
 template <bool TET, int NT, int E, int SW, int SH, int MINB>
-static cudaError_t launch_variant(const FusedArgs &a, int grid, bool record, cudaStream_t st) {
+static cudaError_t launch_variant(const FusedArgs &a, int grid, cudaStream_t st) {
     using Sh = FusedShape<NT, SW, SH>;
     cudaError_t e = ensure_attrs<TET, NT, E, SW, SH, MINB>();
     if (e != cudaSuccess) return e;
-    if (record)
-        k_fused<TET, NT, E, SW, SH, MINB, true><<<grid, NT, Sh::smem, st>>>(a);
-    else
-        k_fused<TET, NT, E, SW, SH, MINB, false><<<grid, NT, Sh::smem, st>>>(a);
+    k_fused<TET, NT, E, SW, SH, MINB><<<grid, NT, Sh::smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -687,7 +659,7 @@ static int blocks_per_sm() {
     using Sh = FusedShape<NT, SW, SH>;
     int n = 0;
     if (ensure_attrs<TET, NT, E, SW, SH, MINB>() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<TET, NT, E, SW, SH, MINB, false>, NT, Sh::smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<TET, NT, E, SW, SH, MINB>, NT, Sh::smem) !=
         cudaSuccess)
         return 0;
     return n;
@@ -702,9 +674,9 @@ static int blocks_per_sm() {
     X(0, 512, 1, 36, 24, 2) X(1, 1024, 1, 68, 24, 1) X(2, 256, 1, 36, 14, 3) X(3, 256, 2, 36, 24, 2)
 
 template <bool TET>
-cudaError_t launch_fused_lattice(int v, const FusedArgs &a, int grid, bool record, cudaStream_t st) {
+cudaError_t launch_fused_lattice(int v, const FusedArgs &a, int grid, cudaStream_t st) {
 #define X(I, NT, E, SW, SH, MINB) \
-    if (v == I) return launch_variant<TET, NT, E, SW, SH, MINB>(a, grid, record, st);
+    if (v == I) return launch_variant<TET, NT, E, SW, SH, MINB>(a, grid, st);
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -62,6 +62,59 @@ cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const Replic
     return cudaGetLastError();
 }
 
+// Per-grain sums of the FP32 state after a block of G steps from ctl->step (the new state is
+// in buffer (step + G) mod 2): every magnetic slot adds its spin, rounded to a multiple of 2^-24,
+// to its grain's 64-bit fixed-point sums.  One warp takes one item (up to 32 runs of one grain):
+// lane k holds run k's descriptor; each run is read by the lanes of the warp in one coalesced
+// pass per component; a lane's partial sums (at most 32 sites of magnitude <= 2^24) fit in 32
+// bits; the warp reduces them in 64 bits and adds them to the grain once.  The sums are
+// integers, so the result does not depend on the order of the additions.
+__global__ void __launch_bounds__(PLAIN_BLOCK) k_grain_sums_fx(
+    const float *__restrict__ S0, const float *__restrict__ S1, long long NS,
+    const unsigned long long *__restrict__ runs, const GrainRunItem *__restrict__ items, int n_items,
+    const Ctl *__restrict__ ctl, int G, unsigned long long *__restrict__ grain_fx) {
+    const int w = blockIdx.x * (PLAIN_BLOCK / 32) + (threadIdx.x >> 5);
+    if (w >= n_items) return;   // uniform over the warp
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const GrainRunItem it = items[w];
+    const unsigned long long mine = lane < it.n_runs ? runs[it.run0 + lane] : 0ull;
+    const float *__restrict__ S = ((ctl->step + G) & 1) ? S1 : S0;
+    int sx = 0, sy = 0, sz = 0;
+#pragma unroll 4
+    for (int k = 0; k < it.n_runs; ++k) {
+        const unsigned long long rw = __shfl_sync(full, mine, k);
+        const long long j = (long long)(rw >> 5) + lane;
+        if (lane <= (int)(rw & 31ull)) {
+            sx += __float2int_rn(S[j] * FX_SCALE);
+            sy += __float2int_rn(S[NS + j] * FX_SCALE);
+            sz += __float2int_rn(S[2 * NS + j] * FX_SCALE);
+        }
+    }
+    long long tx = sx, ty = sy, tz = sz;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tx += __shfl_xor_sync(full, tx, o);
+        ty += __shfl_xor_sync(full, ty, o);
+        tz += __shfl_xor_sync(full, tz, o);
+    }
+    if (lane == 0) {
+        atomicAdd(grain_fx + 3 * (long long)it.grain + 0, (unsigned long long)tx);
+        atomicAdd(grain_fx + 3 * (long long)it.grain + 1, (unsigned long long)ty);
+        atomicAdd(grain_fx + 3 * (long long)it.grain + 2, (unsigned long long)tz);
+    }
+}
+
+cudaError_t launch_grain_sums_fx(const float *S0, const float *S1, long long NS, const unsigned long long *runs,
+                                 const GrainRunItem *items, int n_items, const Ctl *ctl, int G,
+                                 unsigned long long *grain_fx, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const int per = PLAIN_BLOCK / 32;
+    k_grain_sums_fx<<<(unsigned)((n_items + per - 1) / per), PLAIN_BLOCK, 0, st>>>(S0, S1, NS, runs, items, n_items,
+                                                                               ctl, G, grain_fx);
+    return cudaGetLastError();
+}
+
 template <typename Real>
 __global__ void k_aos_to_soa(const double *src, Real *S, long long NS, const ReplicaDev *reps, int r,
                              const uint16_t *gcode, long long n) {
