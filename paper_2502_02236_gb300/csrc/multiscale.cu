@@ -92,15 +92,22 @@ __device__ __forceinline__ V3<Real> field_at(const MsDev &P, const Field<Real> &
     return {F.bx * Pz + F.bxs * Px, F.by * Pz, F.bz * Pz};
 }
 
-__device__ __forceinline__ double langevin(double x) {
-    if (fabs(x) < 1e-3) return x / 3.0 - x * x * x / 45.0 + 2.0 * x * x * x * x * x / 945.0;
-    return 1.0 / tanh(x) - 1.0 / x;
-}
-
-__device__ __forceinline__ double langevin_d(double x) {
-    if (fabs(x) < 1e-3) return 1.0 / 3.0 - x * x / 15.0 + 2.0 * x * x * x * x / 189.0;
-    const double s = sinh(x);
-    return 1.0 / (x * x) - 1.0 / (s * s);
+// The Langevin function L(x) = coth x - 1/x and its derivative L'(x) = 1/x^2 - 1/sinh^2 x
+// from one expm1: with u = expm1(-2|x|) in (-1, 0), coth|x| = (2 + u) / (-u) and
+// 1/sinh^2 x = 4 (1 + u) / u^2.  Below |x| = 1e-3 both come from their Taylor series.
+__device__ __forceinline__ void langevin2(double x, double &L, double &Lp) {
+    const double ax = fabs(x);
+    if (ax < 1e-3) {
+        const double x2 = x * x;
+        L = x / 3.0 - x * x2 / 45.0 + 2.0 * x * x2 * x2 / 945.0;
+        Lp = 1.0 / 3.0 - x2 / 15.0 + 2.0 * x2 * x2 / 189.0;
+        return;
+    }
+    const double u = expm1(-2.0 * ax);
+    const double iu = 1.0 / u, ix = 1.0 / ax;
+    const double l = -(2.0 + u) * iu - ix;
+    L = x < 0.0 ? -l : l;
+    Lp = ix * ix - 4.0 * (1.0 + u) * (iu * iu);
 }
 
 // m_e(T): the largest root in [0, 1] of m = L(3 T_C m / T + mu_s B / (kB T)).  Newton steps
@@ -115,12 +122,14 @@ __device__ double me_root(double T_C, double T, double mu_s, double B, double m0
     const double a = 3.0 * T_C / T, b = mu_s * B / (KB * T);
     double lo = 0.0, hi = 1.0, m = (m0 > 0.0 && m0 <= 1.0) ? m0 : 1.0;
     for (int it = 0; it < 300; ++it) {
-        const double g = langevin(a * m + b) - m;
+        double L, Lp;
+        langevin2(a * m + b, L, Lp);
+        const double g = L - m;
         if (g >= 0.0)
             lo = m;
         else
             hi = m;
-        const double gp = a * langevin_d(a * m + b) - 1.0;
+        const double gp = a * Lp - 1.0;
         const double mn = m - g / gp;
         if (fabs(mn - m) <= 1e-13 * (1.0 + m)) return mn;
         m = (mn > lo && mn < hi) ? mn : 0.5 * (lo + hi);
