@@ -49,6 +49,7 @@ struct MsDev {
     unsigned key0, key1;       // Philox key = seed (low, high)
     int profile;               // write field: 0 uniform, 1 tanh profiles following the head
     double pwz, pdz, pBx0, pwx, pdx;  // profile widths, offsets from the head [m], in-plane amplitude [T]
+    double cA, cK, mu_kB, i3TC;       // 2 A0 / Ms0, 2 K0 / Ms0, mu_s / kB, 1 / (3 T_C)
 };
 
 // The write field at one step, from the host: B0 s(t) dir, Bx0 s(t) and the head position.
@@ -111,15 +112,16 @@ __device__ __forceinline__ void langevin2(double x, double &L, double &Lp) {
 }
 
 // m_e(T): the largest root in [0, 1] of m = L(3 T_C m / T + mu_s B / (kB T)).  Newton steps
-// from m0 (the cell's value at the previous step; 1 when there is none) kept inside a bracket
+// from m0 (extrapolated from the cell's last two solves; 1 when there is none) kept inside a bracket
 // [lo, hi] with L(.) - m >= 0 at lo and < 0 at hi; a step that leaves the bracket is
 // replaced by bisection.  A Newton step below 1e-13 (1 + m) is taken as converged (the
 // iteration is quadratic there; the bound is absolute for small m, where coth x - 1/x loses
 // digits to cancellation and the residual is only known to about 1e-14), before the bracket
 // test, which a converged step can fail by rounding.
-__device__ double me_root(double T_C, double T, double mu_s, double B, double m0) {
+__device__ double me_root(double T_C, double T, double mu_kB, double B, double m0) {
     if (!(T > 0.0)) return 1.0;
-    const double a = 3.0 * T_C / T, b = mu_s * B / (KB * T);
+    const double iT = 1.0 / T;
+    const double a = 3.0 * T_C * iT, b = mu_kB * B * iT;
     double lo = 0.0, hi = 1.0, m = (m0 > 0.0 && m0 <= 1.0) ? m0 : 1.0;
     for (int it = 0; it < 300; ++it) {
         double L, Lp;
@@ -298,14 +300,16 @@ __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real
 }
 
 // Per magnetic cell at time t (FP64): the laser temperature at the cell centre, m_e(T, |B_app|)
-// starting from the cell's previous m_e, and the cell's field and damping coefficients
+// starting from 2 m_e - m_e' (m_e and m_e' the cell's last two solves; m_e alone when that
+// leaves (0, 1] or there is no m_e'): the changes from step to step are smooth, so the first
+// Newton step is usually already below the convergence bound.  Then the cell's field and damping coefficients
 // 2 A(T)/Ms(T) = 2 A0 m_e / Ms0, 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0, alpha = lambda (1 - T/3T_C)
 // with T held in [0, T_C], stored in the arithmetic of the state.  A cell whose temperature
 // and field magnitude equal those of its last solve (Bm == Bm_last, T == Tq) keeps its values:
 // far from the spot T is the ambient temperature to the last bit.
 template <typename Real>
-__global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, MsDev P, ReplicaDev D, double t,
-                          Field<double> F, double Bm_last) {
+__global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, const int *grain, MsDev P,
+                          ReplicaDev D, double t, Field<double> F, double Bm_last) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
     const int q = cell_at(P, cx, cy, cz);
@@ -315,14 +319,18 @@ __global__ void k_mm_prep(double *me, double *Tq, Real *coef, const int *grain, 
     const double Bm = sqrt(B.x * B.x + B.y * B.y + B.z * B.z);
     if (!P.profile && Bm == Bm_last && T == Tq[q]) return;
     Tq[q] = T;
-    const double e = me_root(P.T_C, T, P.mu_s, Bm, me[q]);
+    const double e0 = me[q], ep = me_prev[q];
+    double m0 = 2.0 * e0 - ep;
+    if (!(m0 > 0.0 && m0 <= 1.0)) m0 = e0;
+    const double e = me_root(P.T_C, T, P.mu_kB, Bm, m0);
+    me_prev[q] = e0;
     me[q] = e;
-    double cex = 2.0 * P.A0 * e * e / (P.Ms0 * e), cK = 2.0 * P.K0 * e * e * e / (P.Ms0 * e);
+    double cex = P.cA * e, cK = P.cK * e * e;
     if (!(e > 0.0)) cex = cK = 0.0;
     const double Tc = fmax(fmin(T, P.T_C), 0.0);
     coef[q] = (Real)cex;
     coef[P.nc + q] = (Real)cK;
-    coef[2 * P.nc + q] = (Real)(P.lambda * (1.0 - Tc / (3.0 * P.T_C)));
+    coef[2 * P.nc + q] = (Real)(P.lambda * (1.0 - Tc * P.i3TC));
 }
 
 // One RK4 stage on the evolved cells: K = dm/dt at the stage values Vin, acc += w K and
@@ -602,6 +610,7 @@ struct hamr_ms_ctx {
     void *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *coef = nullptr;
     void *S = nullptr, *S2 = nullptr, *Sp = nullptr, *F1 = nullptr, *BTH = nullptr;
     double *me = nullptr;         // m_e per cell (FP64)
+    double *me_prev = nullptr;    // m_e of each cell's solve before the last one (NaN: none)
     double *Tq = nullptr;         // temperature of each cell's last m_e solve (NaN: none)
     double Bm_last = NAN;         // field magnitude of the last m_e solve
     double *stage = nullptr;      // AoS FP64 staging for host copies
@@ -673,9 +682,11 @@ void ms_free(hamr_ms_t h) {
         h->plans = false;
     }
     if (h->me) cudaFree(h->me);
+    if (h->me_prev) cudaFree(h->me_prev);
     if (h->Tq) cudaFree(h->Tq);
     if (h->stage) cudaFree(h->stage);
     h->me = nullptr;
+    h->me_prev = nullptr;
     h->Tq = nullptr;
     h->stage = nullptr;
     if (h->grain_d) cudaFree(h->grain_d);
@@ -910,7 +921,7 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
     // m_e(T) of every cell at t, then the cone of each thermalised site from its cell's m_e
     const double Bm = field_magnitude_host(h, t);
     k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, h->P.ncz), BLK3, 0, h->stream>>>(
-        h->me, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last);
+        h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last);
     h->Bm_last = Bm;
     k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
                                                           h->ox, cx0, cx1, (unsigned long long)h->events);
@@ -948,8 +959,8 @@ int ms_step(hamr_ms_t h) {
     // m_e(T) of every cell at t_n, then (optionally) the demagnetising field of the state at t_n
     const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t, field_of<double>(h, t),
-                                         h->Bm_last);
+    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t,
+                                         field_of<double>(h, t), h->Bm_last);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
     const Real *Bd = nullptr;
@@ -1063,6 +1074,10 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     P.Ms0 = d->Ms0; P.A0 = d->A0; P.K0 = d->K0;
     P.lambda = d->lambda; P.T_C = d->T_C; P.gamma = d->gamma; P.dt = d->dt;
     P.sig0 = sqrt(2.0 * d->lambda * KB / (d->gamma * d->mu_s * d->dt));
+    P.cA = 2.0 * d->A0 / d->Ms0;
+    P.cK = 2.0 * d->K0 / d->Ms0;
+    P.mu_kB = d->mu_s / KB;
+    P.i3TC = 1.0 / (3.0 * d->T_C);
     P.key0 = (unsigned)d->seed;
     P.key1 = (unsigned)(d->seed >> 32);
     h->D.dir[2] = 1.0;
@@ -1083,6 +1098,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     for (void **b : bufs3c)
         if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me, sizeof(double) * nc);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->me_prev, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->Tq, sizeof(double) * nc);
     void **bufs3w[] = {&h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
     for (void **b : bufs3w)
@@ -1094,6 +1110,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->grain_d, 0, sizeof(int) * nc, h->stream);
     if (e == cudaSuccess) {
         k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->me, 1.0, nc);
+        k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->me_prev, NAN, nc);
         k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->Tq, NAN, nc);
         e = cudaGetLastError();
     }
