@@ -50,6 +50,7 @@ struct MsDev {
     int profile;               // write field: 0 uniform, 1 tanh profiles following the head
     double pwz, pdz, pBx0, pwx, pdx;  // profile widths, offsets from the head [m], in-plane amplitude [T]
     double cA, cK, mu_kB, i3TC;       // 2 A0 / Ms0, 2 K0 / Ms0, mu_s / kB, 1 / (3 T_C)
+    double J_mu, ku2_mu;              // J / mu_s, 2 ku / mu_s
 };
 
 // The write field at one step, from the host: B0 s(t) dir, Bx0 s(t) and the head position.
@@ -191,40 +192,64 @@ __global__ void k_ms_average(Real *m, const Real *S, const int *grain, MsDev P, 
     m[2 * P.nc + q] = nn > Real(0) ? sz / nn : Real(0);
 }
 
-// Exchange sum sum_j J v_j of window site (i, j, k) of grain g over its same-grain bonds: the
-// window spins V inside, the cells m across the window's x faces.
+// Sum of the neighbour directions v_j of window site (i, j, k) of grain g (cell qs) over its
+// same-grain bonds: the window spins V inside, the cells m across the window's x faces.  A
+// neighbour in the site's own cell is of grain g; only a neighbour across a cell face looks
+// up its grain, at cell qs +- 1, +- ncx or +- ncx ncy.  The caller scales the sum by J / mu_s.
 template <typename Real, int RT>
 __device__ __forceinline__ V3<Real> exchange(const MsDev &P, const Real *V, const Real *m, const int *grain, int ox,
-                                             int i, int j, int k, int g) {
-    const Real J = (Real)P.J;
+                                             int i, int j, int k, int g, int qs, long long s) {
+    const int r = RT ? RT : P.r;
+    const long long sy = P.nxw, sz = (long long)P.nxw * P.nyw;
+    const int cy = P.ncx, cz = P.ncx * P.ncy;
     Real ex = 0, ey = 0, ez = 0;
-    const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-#pragma unroll
-    for (int b = 0; b < 6; ++b) {
-        const int ii = i + off[b][0], jj = j + off[b][1], kk = k + off[b][2];
-        if (jj < 0 || jj >= P.nyw || kk < 0 || kk >= P.nzw) continue;
-        Real vx, vy, vz;
-        if (ii >= 0 && ii < P.nxw) {
-            if (grain[cell_at(P, ox + per_cell<RT>(P, ii), per_cell<RT>(P, jj), per_cell<RT>(P, kk))] != g) continue;
-            const long long s = ii + (long long)P.nxw * (jj + (long long)P.nyw * kk);
-            vx = V[s];
-            vy = V[P.nw + s];
-            vz = V[2 * P.nw + s];
-        } else {
-            const int cx = ox + (ii < 0 ? -1 : P.wx);
-            if (cx < 0 || cx >= P.ncx) continue;
-            const int q = cell_at(P, cx, per_cell<RT>(P, jj), per_cell<RT>(P, kk));
-            if (grain[q] != g) continue;
-            vx = m[q];
-            vy = m[P.nc + q];
-            vz = m[2 * P.nc + q];
-        }
-        ex += J * vx;
-        ey += J * vy;
-        ez += J * vz;
-    }
+    auto site = [&](long long t) {
+        ex += V[t];
+        ey += V[P.nw + t];
+        ez += V[2 * P.nw + t];
+    };
+    auto cell = [&](int q) {
+        if (grain[q] != g) return;
+        ex += m[q];
+        ey += m[P.nc + q];
+        ez += m[2 * P.nc + q];
+    };
+    // -x: inside the cell, the next cell of the window, or the interface cell ox - 1
+    if (i % r)
+        site(s - 1);
+    else if (i > 0) {
+        if (grain[qs - 1] == g) site(s - 1);
+    } else if (ox > 0)
+        cell(qs - 1);
+    // +x
+    if ((i + 1) % r)
+        site(s + 1);
+    else if (i + 1 < P.nxw) {
+        if (grain[qs + 1] == g) site(s + 1);
+    } else if (ox + P.wx < P.ncx)
+        cell(qs + 1);
+    // -y, +y, -z, +z: open faces of the track
+    if (j % r)
+        site(s - sy);
+    else if (j > 0 && grain[qs - cy] == g)
+        site(s - sy);
+    if ((j + 1) % r)
+        site(s + sy);
+    else if (j + 1 < P.nyw && grain[qs + cy] == g)
+        site(s + sy);
+    if (k % r)
+        site(s - sz);
+    else if (k > 0 && grain[qs - cz] == g)
+        site(s - sz);
+    if ((k + 1) % r)
+        site(s + sz);
+    else if (k + 1 < P.nzw && grain[qs + cz] == g)
+        site(s + sz);
     return {ex, ey, ez};
 }
+
+__device__ __forceinline__ float inv_norm(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
 
 template <typename Real, int RT>
 __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const Real *m, const int *grain, MsDev P,
@@ -238,7 +263,7 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
         Sp[s] = Sp[P.nw + s] = Sp[2 * P.nw + s] = Real(0);
         return;
     }
-    const Real t = (Real)step * (Real)P.dt, a = (Real)P.a, mu = (Real)P.mu_s;
+    const Real t = (Real)step * (Real)P.dt, a = (Real)P.a;
     const Real T = temp_at(D, ((Real)ox * P.r + i + Real(0.5)) * a, (j + Real(0.5)) * a, t);
     const Real sig = (Real)P.sig0 * sqrt(T);
     const unsigned long long X = (unsigned long long)ox * P.r + i, NX = (unsigned long long)P.ncx * P.r;
@@ -255,19 +280,20 @@ __global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const
         ba.y += Bd[P.nc + qs];
         ba.z += Bd[2 * P.nc + qs];
     }
-    const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g);
+    const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g, qs, s);
+    const Real Jm = (Real)P.J_mu, Km = (Real)P.ku2_mu;
     const Real sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
-    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, ex.x / mu + ba.x + bthx,
-                                 ex.y / mu + ba.y + bthy, ex.z / mu + Real(2) * (Real)P.ku / mu * sz + ba.z + bthz);
+    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, Jm * ex.x + ba.x + bthx,
+                                 Jm * ex.y + ba.y + bthy, Jm * ex.z + Km * sz + ba.z + bthz);
     F1[s] = f.x;
     F1[P.nw + s] = f.y;
     F1[2 * P.nw + s] = f.z;
     const Real dt = (Real)P.dt;
     const Real vx = sx + dt * f.x, vy = sy + dt * f.y, vz = sz + dt * f.z;
-    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
-    Sp[s] = vx / nv;
-    Sp[P.nw + s] = vy / nv;
-    Sp[2 * P.nw + s] = vz / nv;
+    const Real in = inv_norm(vx * vx + vy * vy + vz * vz);
+    Sp[s] = vx * in;
+    Sp[P.nw + s] = vy * in;
+    Sp[2 * P.nw + s] = vz * in;
 }
 
 template <typename Real, int RT>
@@ -279,58 +305,73 @@ __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real
     const int qs = cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k));
     const int g = grain[qs];
     if (g < 0) return;
-    const Real mu = (Real)P.mu_s, dt = (Real)P.dt;
+    const Real dt = (Real)P.dt;
     V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * (Real)P.a);
     if (Bd) {
         ba.x += Bd[qs];
         ba.y += Bd[P.nc + qs];
         ba.z += Bd[2 * P.nc + qs];
     }
-    const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g);
+    const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g, qs, s);
+    const Real Jm = (Real)P.J_mu, Km = (Real)P.ku2_mu;
     const Real px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
-    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, ex.x / mu + ba.x + BTH[s],
-                                 ex.y / mu + ba.y + BTH[P.nw + s],
-                                 ex.z / mu + Real(2) * (Real)P.ku / mu * pz + ba.z + BTH[2 * P.nw + s]);
+    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, Jm * ex.x + ba.x + BTH[s],
+                                 Jm * ex.y + ba.y + BTH[P.nw + s], Jm * ex.z + Km * pz + ba.z + BTH[2 * P.nw + s]);
     const Real vx = S[s] + Real(0.5) * dt * (F1[s] + f.x), vy = S[P.nw + s] + Real(0.5) * dt * (F1[P.nw + s] + f.y),
                vz = S[2 * P.nw + s] + Real(0.5) * dt * (F1[2 * P.nw + s] + f.z);
-    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
-    S[s] = vx / nv;
-    S[P.nw + s] = vy / nv;
-    S[2 * P.nw + s] = vz / nv;
+    const Real in = inv_norm(vx * vx + vy * vy + vz * vz);
+    S[s] = vx * in;
+    S[P.nw + s] = vy * in;
+    S[2 * P.nw + s] = vz * in;
 }
 
-// Per magnetic cell at time t (FP64): the laser temperature at the cell centre, m_e(T, |B_app|)
-// starting from 2 m_e - m_e' (m_e and m_e' the cell's last two solves; m_e alone when that
-// leaves (0, 1] or there is no m_e'): the changes from step to step are smooth, so the first
-// Newton step is usually already below the convergence bound.  Then the cell's field and damping coefficients
-// 2 A(T)/Ms(T) = 2 A0 m_e / Ms0, 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0, alpha = lambda (1 - T/3T_C)
-// with T held in [0, T_C], stored in the arithmetic of the state.  A cell whose temperature
-// and field magnitude equal those of its last solve (Bm == Bm_last, T == Tq) keeps its values:
-// far from the spot T is the ambient temperature to the last bit.
+// Per column (cx, cy) of magnetic cells at time t (FP64): the laser temperature at the column's
+// centre and the write field depend on (x, y) only, so every cell of the column has the same
+// m_e(T, |B_app|), solved once.  Newton starts from 2 m_e - m_e' (m_e and m_e' the last two
+// solves of the column's first magnetic cell; m_e alone when that leaves (0, 1] or there is no
+// m_e'): the changes from step to step are smooth, so the first Newton step is usually already
+// below the convergence bound.  Every magnetic cell of the column then gets m_e, its history
+// and its field and damping coefficients 2 A(T)/Ms(T) = 2 A0 m_e / Ms0,
+// 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0, alpha = lambda (1 - T/3T_C) with T held in [0, T_C],
+// stored in the arithmetic of the state.  A column whose cells all solved last at this
+// temperature and field magnitude (Bm == Bm_last, T == Tq) keeps its values: far from the
+// spot T is the ambient temperature to the last bit.
 template <typename Real>
 __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, const int *grain, MsDev P,
                           ReplicaDev D, double t, Field<double> F, double Bm_last) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
-    const int q = cell_at(P, cx, cy, cz);
-    if (grain[q] < 0) return;
+    const int q0 = cell_at(P, cx, cy, 0), lz = P.ncx * P.ncy;
     const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
     const V3<double> B = field_at(P, F, (cx + 0.5) * P.cell);
     const double Bm = sqrt(B.x * B.x + B.y * B.y + B.z * B.z);
-    if (!P.profile && Bm == Bm_last && T == Tq[q]) return;
-    Tq[q] = T;
-    const double e0 = me[q], ep = me_prev[q];
+    int first = -1;
+    bool same = !P.profile && Bm == Bm_last;
+    for (int z = 0; z < P.ncz; ++z) {
+        const int q = q0 + z * lz;
+        if (grain[q] < 0) continue;
+        if (first < 0) first = q;
+        same = same && T == Tq[q];
+    }
+    if (first < 0 || same) return;
+    const double e0 = me[first], ep = me_prev[first];
     double m0 = 2.0 * e0 - ep;
     if (!(m0 > 0.0 && m0 <= 1.0)) m0 = e0;
     const double e = me_root(P.T_C, T, P.mu_kB, Bm, m0);
-    me_prev[q] = e0;
-    me[q] = e;
     double cex = P.cA * e, cK = P.cK * e * e;
     if (!(e > 0.0)) cex = cK = 0.0;
     const double Tc = fmax(fmin(T, P.T_C), 0.0);
-    coef[q] = (Real)cex;
-    coef[P.nc + q] = (Real)cK;
-    coef[2 * P.nc + q] = (Real)(P.lambda * (1.0 - Tc * P.i3TC));
+    const Real rex = (Real)cex, rK = (Real)cK, ral = (Real)(P.lambda * (1.0 - Tc * P.i3TC));
+    for (int z = 0; z < P.ncz; ++z) {
+        const int q = q0 + z * lz;
+        if (grain[q] < 0) continue;
+        Tq[q] = T;
+        me_prev[q] = me[q];
+        me[q] = e;
+        coef[q] = rex;
+        coef[P.nc + q] = rK;
+        coef[2 * P.nc + q] = ral;
+    }
 }
 
 // One RK4 stage on the evolved cells: K = dm/dt at the stage values Vin, acc += w K and
@@ -346,17 +387,20 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
     Real lx = 0, ly = 0, lz = 0;
     const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-    const Real c2 = (Real)(P.cell * P.cell);
+    const Real ic2 = (Real)(1.0 / (P.cell * P.cell));
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
         const int x = cx + off[b][0], y = cy + off[b][1], z = cz + off[b][2];
         if (x < 0 || x >= P.ncx || y < 0 || y >= P.ncy || z < 0 || z >= P.ncz) continue;
         const int qn = cell_at(P, x, y, z);
         if (grain[qn] != grain[q]) continue;
-        lx += (Vin[qn] - vx) / c2;
-        ly += (Vin[P.nc + qn] - vy) / c2;
-        lz += (Vin[2 * P.nc + qn] - vz) / c2;
+        lx += Vin[qn] - vx;
+        ly += Vin[P.nc + qn] - vy;
+        lz += Vin[2 * P.nc + qn] - vz;
     }
+    lx *= ic2;
+    ly *= ic2;
+    lz *= ic2;
     const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
     const V3<Real> ba = field_at(P, F, (Real)((cx + 0.5) * P.cell));
     Real bx = ba.x, by = ba.y, bz = ba.z;
@@ -920,7 +964,7 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
     if (n <= 0) return HAMR_OK;
     // m_e(T) of every cell at t, then the cone of each thermalised site from its cell's m_e
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, h->P.ncz), BLK3, 0, h->stream>>>(
+    k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, 1), BLK3, 0, h->stream>>>(
         h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last);
     h->Bm_last = Bm;
     k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
@@ -959,8 +1003,8 @@ int ms_step(hamr_ms_t h) {
     // m_e(T) of every cell at t_n, then (optionally) the demagnetising field of the state at t_n
     const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<gc, BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P, h->D, t,
-                                         field_of<double>(h, t), h->Bm_last);
+    k_mm_prep<Real><<<grid3(P.ncx, P.ncy, 1), BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P,
+                                                            h->D, t, field_of<double>(h, t), h->Bm_last);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
     const Real *Bd = nullptr;
@@ -1078,6 +1122,8 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     P.cK = 2.0 * d->K0 / d->Ms0;
     P.mu_kB = d->mu_s / KB;
     P.i3TC = 1.0 / (3.0 * d->T_C);
+    P.J_mu = d->J / d->mu_s;
+    P.ku2_mu = 2.0 * d->ku / d->mu_s;
     P.key0 = (unsigned)d->seed;
     P.key1 = (unsigned)(d->seed >> 32);
     h->D.dir[2] = 1.0;
