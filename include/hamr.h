@@ -118,8 +118,10 @@ int hamr_set_csr(hamr_t h, int32_t replica, const int32_t *row_ptr, const int32_
 
 /* Grain map of one replica (Sec. II: exchange-decoupled grains): grain[n] with ids in
  * [0, n_grains) or -1 for a non-magnetic site.  Exchange bonds join only sites of the
- * same grain; spins of non-magnetic sites are set to 0.  n_grains <= 65534.
- * Errors: ARG. */
+ * same grain; spins of non-magnetic sites are set to 0.  A site that turns magnetic keeps
+ * its stored spin, which is 0 if it was non-magnetic: after changing a map in the middle
+ * of a run, set the replica's moments (hamr_set_moments) before the next step.
+ * n_grains <= 65534.  Errors: ARG. */
 int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t n_grains);
 
 /* Laser temperature of one replica (Sec. III, Fig. 2):

@@ -1073,6 +1073,9 @@ int hamr_set_grain_map(hamr_t h, int32_t replica, const int32_t *grain, int32_t 
     R.cross_grain = cross;
     h->n_grains[replica] = n_grains;
     count_grains(h, replica);
+    // the fused path lists only columns that hold a magnetic site: rebuild its work list
+    h->items_dirty = true;
+    clear_graphs(h);
     const long long span = (long long)R.px * R.ny * R.nz;
     CK(h, cudaMemcpyAsync(h->gcode_d + R.off, h->gcode_h.data() + R.off, sizeof(uint16_t) * span,
                           cudaMemcpyHostToDevice, h->stream));

@@ -323,6 +323,43 @@ def test_grain_averages_and_energy(prec, tol):
     assert abs(E - Eo) <= (1e-9 if prec == "fp64" else 2e-4) * abs(Eo)
 
 
+def test_fp32_grain_records_batched_and_after_grain_change():
+    """Per-grain record sums of the FP32 fused path over a batch: granular replicas, one
+    replica of a single grain (rows of 70 sites, so runs of 32, 32 and 6 slots, and one grain
+    spanning many warp items), then again after one replica's grain map changes between record
+    points (the runs are rebuilt)."""
+    reps = [tiny_track(48, 40, 6, seed=4), tiny_track(70, 33, 4, seed=6, grains=False), tiny_track(45, 37, 5, seed=8)]
+    w = workload_of(reps)
+    S = [initial(rep) for rep in reps]
+    lat = gpu_lattice(w, S0=S)
+
+    def check(step0, n):
+        for r, rep in enumerate(w["replicas"]):
+            o = oracle_for(w, r)
+            o.run(S[r], step0, n)
+            M, steps, Mg = lat.read_magnetisation(r, rep["n_grains"])
+            assert steps[-1] == step0 + n
+            sums, counts = o.grain_sums(S[r], rep["n_grains"])
+            want = np.where(counts[:, None] > 0, sums / np.maximum(counts[:, None], 1), 0.0)
+            assert max_abs(Mg, want) < TOL32, (r, max_abs(Mg, want))
+            assert max_abs(M[-1], o.magnetisation(S[r])) < TOL32
+
+    lat.sllg_heun_steps(40, 20)
+    check(0, 40)
+    a = w["a"]
+    g2 = I.voronoi_grains(45, 37, a, a, 4e-9, 0.5e-9, 99)
+    grain = I.columnar(g2, 5)
+    w["replicas"][2] = dict(reps[2], grain=grain, n_grains=int(g2.max()) + 1)
+    lat.set_grain_map(2, grain, int(g2.max()) + 1)
+    # sites that turn magnetic had no spin: give them +z on both sides
+    S2 = S[2].reshape(-1, 3).copy()
+    S2[np.all(S2 == 0.0, axis=1)] = (0.0, 0.0, 1.0)
+    S[2] = np.ascontiguousarray(I.mask_void(S2, grain).reshape(S[2].shape))
+    lat.set_moments(2, S[2])
+    lat.sllg_heun_steps(40, 20)
+    check(40, 40)
+
+
 # --------------------------------------------------------------------------- state handling
 def test_checkpoint_resume_bitwise(tmp_path):
     w = workload_of(uneven_replicas()[:4])
