@@ -168,7 +168,7 @@ __device__ __forceinline__ bool coords(int nx, int ny, int &x, int &y, int &z) {
 
 // Eq. 6 for the cells of columns [cx0, cx0 + ncol): direction of the sum of their sites.
 template <typename Real>
-__global__ void k_ms_average(Real *m, const Real *S, const int *grain, MsDev P, int ox, int cx0, int ncol) {
+__global__ void k_ms_average(Real *m, Real *wn, const Real *S, const int *grain, MsDev P, int ox, int cx0, int ncol) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n = (long long)ncol * P.ncy * P.ncz;
     if (idx >= n) return;
@@ -190,6 +190,52 @@ __global__ void k_ms_average(Real *m, const Real *S, const int *grain, MsDev P, 
     m[q] = nn > Real(0) ? sx / nn : Real(0);
     m[P.nc + q] = nn > Real(0) ? sy / nn : Real(0);
     m[2 * P.nc + q] = nn > Real(0) ? sz / nn : Real(0);
+    wn[q] = nn;
+}
+
+// The same for a compile-time ratio RT in {1, 2, 4}: a warp takes 32 / RT consecutive cells
+// of one cell row (cy, cz); lane (c, di) sums site column di of cell c over the cell's RT^2
+// rows (dj, dk), each row read by the warp as one run of consecutive sites, and the RT lanes
+// of a cell add by shuffles.
+template <typename Real, int RT>
+__global__ void k_ms_average_w(Real *m, Real *wn, const Real *S, const int *grain, MsDev P, int ox, int cx0,
+                               int ncol) {
+    constexpr int CPW = 32 / RT;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int wpr = (ncol + CPW - 1) / CPW;
+    if (w >= (long long)wpr * P.ncy * P.ncz) return;   // uniform over the warp
+    const int row = (int)(w / wpr), c = (int)(w % wpr) * CPW + lane / RT, di = lane % RT;
+    const int cy = row % P.ncy, cz = row / P.ncy, cx = cx0 + c;
+    const bool act = c < ncol;
+    const int q = act ? cell_at(P, cx, cy, cz) : 0;
+    Real sx = 0, sy = 0, sz = 0;
+    if (act && grain[q] >= 0) {
+        const long long i = (long long)(cx - ox) * RT + di;
+#pragma unroll
+        for (int dk = 0; dk < RT; ++dk)
+#pragma unroll
+            for (int dj = 0; dj < RT; ++dj) {
+                const long long s = i + P.nxw * ((long long)cy * RT + dj + (long long)P.nyw * ((long long)cz * RT + dk));
+                sx += S[s];
+                sy += S[P.nw + s];
+                sz += S[2 * P.nw + s];
+            }
+    }
+#pragma unroll
+    for (int o = RT / 2; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(full, sx, o);
+        sy += __shfl_xor_sync(full, sy, o);
+        sz += __shfl_xor_sync(full, sz, o);
+    }
+    if (act && di == 0) {
+        const Real nn = sqrt(sx * sx + sy * sy + sz * sz);
+        m[q] = nn > Real(0) ? sx / nn : Real(0);
+        m[P.nc + q] = nn > Real(0) ? sy / nn : Real(0);
+        m[2 * P.nc + q] = nn > Real(0) ? sz / nn : Real(0);
+        wn[q] = nn;
+    }
 }
 
 // Sum of the neighbour directions v_j of window site (i, j, k) of grain g (cell qs) over its
@@ -559,9 +605,10 @@ struct Pad {
 };
 
 // The cells' magnetisation in the padded layout: window cells M = (mu_s / V) sum of their
-// spins (Eq. 6), other magnetic cells M = Ms0 m_e m, non-magnetic cells 0.
+// spins (Eq. 6; wn holds the sum's length and m its direction, from the window average of
+// the same state), other magnetic cells M = Ms0 m_e m, non-magnetic cells 0.
 template <typename Real>
-__global__ void k_demag_M(Real *Mpad, const Real *S, const Real *m, const double *me, const int *grain, MsDev P,
+__global__ void k_demag_M(Real *Mpad, const Real *wn, const Real *m, const double *me, const int *grain, MsDev P,
                           Pad pd, int ox) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
@@ -569,24 +616,13 @@ __global__ void k_demag_M(Real *Mpad, const Real *S, const Real *m, const double
     const long long pp = cx + (long long)pd.Px * (cy + (long long)pd.Py * cz);
     Real Mx = 0, My = 0, Mz = 0;
     if (grain[q] >= 0) {
-        if (cx >= ox && cx < ox + P.wx) {
-            const Real scale = (Real)(P.mu_s / (P.cell * P.cell * P.cell));
-            for (int dk = 0; dk < P.r; ++dk)
-                for (int dj = 0; dj < P.r; ++dj)
-                    for (int di = 0; di < P.r; ++di) {
-                        const long long i = (long long)(cx - ox) * P.r + di, j = (long long)cy * P.r + dj,
-                                        k = (long long)cz * P.r + dk;
-                        const long long s = i + P.nxw * (j + (long long)P.nyw * k);
-                        Mx += scale * S[s];
-                        My += scale * S[P.nw + s];
-                        Mz += scale * S[2 * P.nw + s];
-                    }
-        } else {
-            const Real a = (Real)(P.Ms0 * me[q]);
-            Mx = a * m[q];
-            My = a * m[P.nc + q];
-            Mz = a * m[2 * P.nc + q];
-        }
+        // a window cell: (mu_s / V) |sum of its sites| times their direction, both from Eq. 6
+        // of this step; a cell outside: Ms0 m_e(T) m
+        const Real a = (cx >= ox && cx < ox + P.wx) ? (Real)(P.mu_s / (P.cell * P.cell * P.cell)) * wn[q]
+                                                    : (Real)(P.Ms0 * me[q]);
+        Mx = a * m[q];
+        My = a * m[P.nc + q];
+        Mz = a * m[2 * P.nc + q];
     }
     Mpad[pp] = Mx;
     Mpad[pd.Ptot + pp] = My;
@@ -653,6 +689,7 @@ struct hamr_ms_ctx {
     // state-precision planes: cells m, V0, V1, acc, coef [3][nc]; window S, S2, Sp, F1, BTH [3][nw]
     void *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *coef = nullptr;
     void *S = nullptr, *S2 = nullptr, *Sp = nullptr, *F1 = nullptr, *BTH = nullptr;
+    void *wn = nullptr;           // |sum of the sites| of each window cell (Eq. 6), state precision
     double *me = nullptr;         // m_e per cell (FP64)
     double *me_prev = nullptr;    // m_e of each cell's solve before the last one (NaN: none)
     double *Tq = nullptr;         // temperature of each cell's last m_e solve (NaN: none)
@@ -725,10 +762,12 @@ void ms_free(hamr_ms_t h) {
         cufftDestroy(h->plan_b);
         h->plans = false;
     }
+    if (h->wn) cudaFree(h->wn);
     if (h->me) cudaFree(h->me);
     if (h->me_prev) cudaFree(h->me_prev);
     if (h->Tq) cudaFree(h->Tq);
     if (h->stage) cudaFree(h->stage);
+    h->wn = nullptr;
     h->me = nullptr;
     h->me_prev = nullptr;
     h->Tq = nullptr;
@@ -939,7 +978,7 @@ int ms_demag_step(hamr_ms_t h) {
     const MsDev &P = h->P;
     const Pad &pd = h->pad;
     const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
-    k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Mpad, (const Real *)h->S, (const Real *)h->m, h->me,
+    k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Mpad, (const Real *)h->wn, (const Real *)h->m, h->me,
                                                 h->grain_d, P, pd, h->ox);
     MSCK(h, cudaGetLastError());
     const bool dbl = sizeof(Real) == 8;
@@ -976,9 +1015,24 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
 
 template <typename Real>
 int ms_average(hamr_ms_t h, int cx0, int ncol) {
-    const long long n = (long long)ncol * h->P.ncy * h->P.ncz;
-    k_ms_average<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->m, (const Real *)h->S, h->grain_d, h->P, h->ox, cx0,
-                                                       ncol);
+    const MsDev &P = h->P;
+    const long long n = (long long)ncol * P.ncy * P.ncz;
+    Real *m = (Real *)h->m, *wn = (Real *)h->wn;
+    const Real *S = (const Real *)h->S;
+#define MS_AVG(RT)                                                                                       \
+    do {                                                                                                 \
+        const long long nthr = 32LL * ((ncol + 32 / RT - 1) / (32 / RT)) * P.ncy * P.ncz;                \
+        k_ms_average_w<Real, RT><<<nblk(nthr), BLK, 0, h->stream>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol); \
+    } while (0)
+    switch (P.r) {
+        case 1: MS_AVG(1); break;
+        case 2: MS_AVG(2); break;
+        case 4: MS_AVG(4); break;
+        default:
+            k_ms_average<Real><<<nblk(n), BLK, 0, h->stream>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol);
+            break;
+    }
+#undef MS_AVG
     MSCK(h, cudaGetLastError());
     return HAMR_OK;
 }
@@ -1143,6 +1197,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     cudaError_t e = cudaSuccess;
     for (void **b : bufs3c)
         if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&h->wn, el * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me_prev, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->Tq, sizeof(double) * nc);
@@ -1152,6 +1207,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->stage, sizeof(double) * 3 * (nw > nc ? nw : nc));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->grain_d, sizeof(int) * nc);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->m, 0, el * 3 * nc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->wn, 0, el * nc, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, el * 3 * nw, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->grain_d, 0, sizeof(int) * nc, h->stream);
     if (e == cudaSuccess) {
