@@ -421,32 +421,47 @@ __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, c
 }
 
 // One RK4 stage on the evolved cells: K = dm/dt at the stage values Vin, acc += w K and
-// Vout = m + c dt K (the next stage's values).  Cells that are not evolved keep m in both
-// stage buffers.
+// Vout = m + c dt K (the next stage's values).  A window cell writes its Eq. 6 direction m
+// to Vout, so that every stage buffer holds m there (stage 0 reads m itself); non-magnetic
+// cells are never read.  The cell's grain code, its stage value and its neighbours' grain
+// codes are loaded together before the tests: the kernel is one wave of short threads,
+// bound by memory latency.
 template <typename Real>
-__global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first) {
+__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 16 : 10) k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m,
+                                                       const Real *coef, const int *grain, MsDev P, int ox, Field<Real> F,
+                                                       const Real *Bd, Real c, Real w, int first) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
-    const int q = cell_at(P, cx, cy, cz);
-    if (grain[q] < 0 || (cx >= ox && cx < ox + P.wx)) return;   // only the evolved cells
+    const int q = cell_at(P, cx, cy, cz), lz = P.ncx * P.ncy;
+    const int g = grain[q];
     const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
-    Real lx = 0, ly = 0, lz = 0;
-    const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-    const Real ic2 = (Real)(1.0 / (P.cell * P.cell));
+    // neighbours -x, +x, -y, +y, -z, +z (an absent one reads the cell itself and is masked)
+    const bool has[6] = {cx > 0, cx + 1 < P.ncx, cy > 0, cy + 1 < P.ncy, cz > 0, cz + 1 < P.ncz};
+    const int qn[6] = {has[0] ? q - 1 : q, has[1] ? q + 1 : q, has[2] ? q - P.ncx : q,
+                       has[3] ? q + P.ncx : q, has[4] ? q - lz : q, has[5] ? q + lz : q};
+    int gn[6];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) gn[b] = grain[qn[b]];
+    if (g < 0) return;
+    const Real mx = m[q], my = m[P.nc + q], mz = m[2 * P.nc + q];
+    if (cx >= ox && cx < ox + P.wx) {   // a window cell: not evolved here
+        Vout[q] = mx;
+        Vout[P.nc + q] = my;
+        Vout[2 * P.nc + q] = mz;
+        return;
+    }
+    Real lx = 0, ly = 0, lz2 = 0;
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
-        const int x = cx + off[b][0], y = cy + off[b][1], z = cz + off[b][2];
-        if (x < 0 || x >= P.ncx || y < 0 || y >= P.ncy || z < 0 || z >= P.ncz) continue;
-        const int qn = cell_at(P, x, y, z);
-        if (grain[qn] != grain[q]) continue;
-        lx += Vin[qn] - vx;
-        ly += Vin[P.nc + qn] - vy;
-        lz += Vin[2 * P.nc + qn] - vz;
+        if (!has[b] || gn[b] != g) continue;
+        lx += Vin[qn[b]] - vx;
+        ly += Vin[P.nc + qn[b]] - vy;
+        lz2 += Vin[2 * P.nc + qn[b]] - vz;
     }
+    const Real ic2 = (Real)(1.0 / (P.cell * P.cell));
     lx *= ic2;
     ly *= ic2;
-    lz *= ic2;
+    lz2 *= ic2;
     const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
     const V3<Real> ba = field_at(P, F, (Real)((cx + 0.5) * P.cell));
     Real bx = ba.x, by = ba.y, bz = ba.z;
@@ -455,16 +470,16 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
         by += Bd[P.nc + q];
         bz += Bd[2 * P.nc + q];
     }
-    const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz + cK * vz + bz);
+    const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz2 + cK * vz + bz);
     const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
                a2 = first ? Real(0) : acc[2 * P.nc + q];
     acc[q] = a0 + w * k.x;
     acc[P.nc + q] = a1 + w * k.y;
     acc[2 * P.nc + q] = a2 + w * k.z;
     const Real dt = (Real)P.dt;
-    Vout[q] = m[q] + c * dt * k.x;
-    Vout[P.nc + q] = m[P.nc + q] + c * dt * k.y;
-    Vout[2 * P.nc + q] = m[2 * P.nc + q] + c * dt * k.z;
+    Vout[q] = mx + c * dt * k.x;
+    Vout[P.nc + q] = my + c * dt * k.y;
+    Vout[2 * P.nc + q] = mz + c * dt * k.z;
 }
 
 template <typename Real>
@@ -1080,11 +1095,9 @@ int ms_step(hamr_ms_t h) {
     }
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
-    MSCK(h, cudaMemcpyAsync(h->V0, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
-    MSCK(h, cudaMemcpyAsync(h->V1, h->m, sizeof(Real) * 3 * P.nc, cudaMemcpyDeviceToDevice, st));
     const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
     for (int s = 0; s < 4; ++s) {
-        const Real *vin = (const Real *)((s & 1) ? h->V1 : h->V0);
+        const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
         Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
         k_mm_stage<Real><<<gc, BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m, (const Real *)h->coef, h->grain_d, P, h->ox,
                                               F, Bd, cst[s], wst[s], s == 0);
