@@ -424,12 +424,11 @@ __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, c
 // Vout = m + c dt K (the next stage's values).  A window cell writes its Eq. 6 direction m
 // to Vout, so that every stage buffer holds m there (stage 0 reads m itself); non-magnetic
 // cells are never read.  The cell's grain code, its stage value and its neighbours' grain
-// codes are loaded together before the tests: the kernel is one wave of short threads,
-// bound by memory latency.
+// codes are loaded together before the tests: the threads are short and bound by memory
+// latency.
 template <typename Real>
-__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 16 : 10) k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m,
-                                                       const Real *coef, const int *grain, MsDev P, int ox, Field<Real> F,
-                                                       const Real *Bd, Real c, Real w, int first) {
+__global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
+                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first) {
     int cx, cy, cz;
     if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
     const int q = cell_at(P, cx, cy, cz), lz = P.ncx * P.ncy;
