@@ -118,6 +118,8 @@ def lib():
         L.orc_ms_create.argtypes = [MP, vp]
         L.orc_ms_create.restype = vp
         L.orc_ms_destroy.argtypes = [vp]
+        L.orc_ms_set_drivers.argtypes = [vp, MP]
+        L.orc_ms_set_drivers.restype = ctypes.c_int
         L.orc_ms_set_cells.argtypes = [vp, vp]
         L.orc_ms_get_cells.argtypes = [vp, vp]
         L.orc_ms_get_moments.argtypes = [vp, vp]
@@ -469,6 +471,15 @@ class MsOracle:
         if h and _lib is not None:
             _lib.orc_ms_destroy(h)
             self._h = None
+
+    def set_drivers(self, p):
+        """New drivers (laser spot, write field, head profile, demagnetising switch) from the
+        MsParams p of the same track, material, time step and seed, from the next step on."""
+        s = p.struct()
+        if lib().orc_ms_set_drivers(self._h, ctypes.byref(s)) != 0:
+            raise ValueError("the parameters describe another track or material")
+        self.p = p
+        self._s = s
 
     def set_cells(self, m):
         m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1)

@@ -72,6 +72,8 @@ typedef struct {
     double *S;              /* [3 nw] AoS, site (i, j, k) at i + nxw (j + nyw k) */
     int64_t step;           /* completed steps */
     int64_t events;         /* thermalisation events so far (window placements and moves) */
+    int32_t live;           /* 1: the window's sites are newer than its cells (placed, and the
+                               cells not replaced since) */
     double *Bd;             /* [3 nc] demagnetising field of the current step [T], or NULL */
 } orc_ms;
 
@@ -206,10 +208,38 @@ orc_ms *orc_ms_create(const orc_ms_params *p, const int32_t *cell_grain)
     return c;
 }
 
+/* Replaces the drivers of a context between steps, as the library's setters do: the laser
+ * spot, the write field with its bit pattern and head profile, and the switch of the
+ * demagnetising field.  The step count, the window and the state stay.  A second pass along a
+ * parallel track (Sec. III) is a new spot centre y0 and spot and head starting points for the
+ * current time.  Returns -1, and changes nothing, when p describes another track, material,
+ * time step or seed. */
+int orc_ms_set_drivers(orc_ms *c, const orc_ms_params *p)
+{
+    const orc_ms_params *o = &c->p;
+    if (p->ncx != o->ncx || p->ncy != o->ncy || p->ncz != o->ncz || p->cell != o->cell || p->ratio != o->ratio ||
+        p->wx != o->wx || p->J != o->J || p->mu_s != o->mu_s || p->ku != o->ku || p->Ms0 != o->Ms0 ||
+        p->A0 != o->A0 || p->K0 != o->K0 || p->lambda != o->lambda || p->T_C != o->T_C ||
+        p->drv.dt != o->drv.dt || p->drv.gamma != o->drv.gamma || p->drv.seed != o->drv.seed)
+        return -1;
+    uint8_t *bits = NULL;
+    if (p->drv.n_bits > 0) {
+        bits = (uint8_t *)malloc((size_t)p->drv.n_bits);
+        if (!bits) return -1;
+        memcpy(bits, p->drv.bits, (size_t)p->drv.n_bits);
+    }
+    free(c->bits);
+    c->bits = bits;
+    c->p = *p;
+    c->p.drv.bits = bits;
+    return 0;
+}
+
 void orc_ms_set_cells(orc_ms *c, const double *m)
 {
     for (int64_t q = 0; q < c->nc; ++q)
         for (int d = 0; d < 3; ++d) c->m[3 * q + d] = c->grain[q] >= 0 ? m[3 * q + d] : 0.0;
+    c->live = 0;
 }
 
 void orc_ms_get_cells(const orc_ms *c, double *m) { memcpy(m, c->m, sizeof(double) * 3 * (size_t)c->nc); }
@@ -287,10 +317,14 @@ static void thermalise(orc_ms *c, int32_t cx0, int32_t cx1, double t, uint64_t e
             }
 }
 
-/* Place the window at cell column ox and thermalise all of it from the cells. */
+/* Place the window at cell column ox and thermalise all of it from the cells.  A window that
+ * is already placed first hands its sites back to its cells by Eq. 6, as the trailing column
+ * does when the window moves (Sec. II), unless the cells have been replaced since. */
 int orc_ms_set_window(orc_ms *c, int32_t ox)
 {
     if (ox < 0 || ox + c->p.wx > c->p.ncx) return -1;
+    if (c->live) average_cells(c, c->ox, c->ox + c->p.wx);
+    c->live = 1;
     c->ox = ox;
     thermalise(c, ox, ox + c->p.wx, (double)c->step * c->p.drv.dt, (uint64_t)c->events);
     c->events += 1;

@@ -514,6 +514,103 @@ def check_window_target():
     assert o.ms_target(p2, 0.0) == 0
 
 
+def check_set_drivers_continues_run():
+    """Replacing the drivers between steps by the same ones leaves the run bitwise what an
+    uninterrupted run gives (the step count, window and state are kept: the laser keeps moving
+    and the noise keeps its counters); drivers for another track are refused."""
+    kw = dict(J=J_SC, ku=KU, dt=1e-16, T_amb=300.0, T_peak=1200.0, fwhm=4e-9, x0=4.2e-9, y0=1e-9,
+              vx=2e5, B0=1.0, direction=(0.0, 0.0, -1.0), seed=5)
+    p = o.MsParams(16, 2, 1, 2 * A, 2, 4, **kw)
+    a, b = o.MsOracle(p), o.MsOracle(p)
+    m0 = _tilted(p.n_cells, 3, 40.0)
+    for O in (a, b):
+        O.set_cells(m0)
+        O.set_window(o.ms_target(p, 0.0))
+    a.run(30, follow=True)
+    b.run(13, follow=True)
+    b.set_drivers(o.MsParams(16, 2, 1, 2 * A, 2, 4, **kw))
+    b.run(17, follow=True)
+    assert a.step == b.step == 30 and a.window == b.window
+    assert np.array_equal(a.cells(), b.cells()) and np.array_equal(a.moments(), b.moments())
+    try:
+        b.set_drivers(o.MsParams(17, 2, 1, 2 * A, 2, 4, **kw))
+        raise AssertionError("drivers of another track accepted")
+    except ValueError:
+        pass
+
+
+def check_second_pass_keeps_written_tracks():
+    """Two passes along parallel tracks (Sec. III): at T = 0 with no write field, every spin
+    along +z or -z stays exactly there (its field is along z, so there is no torque and no
+    noise), Eq. 6 of a uniform cell returns its direction and a cone of half-angle 0 returns
+    the cell's direction.  So after a first pass along one row band, then new drivers (spot
+    centre on the other band, spot and head restarted at the current time) and a second pass,
+    both written patterns read back exactly and the window follows the new spot."""
+    ncx, ncy, ncz, r, wx, L = 36, 10, 1, 2, 6, 4
+    cell = 2 * A
+    v = 4 * cell / (60 * 1e-16)        # four cells per 60 steps
+    kw = dict(J=J_SC, ku=KU, dt=1e-16, T_amb=0.0, vx=v, B0=0.0, seed=9)
+    p1 = o.MsParams(ncx, ncy, ncz, cell, r, wx, x0=3.2 * cell, y0=2 * cell, **kw)
+    pat1 = [0, 1, 1, 0, 1, 0, 0, 1, 0]
+    pat2 = [1, 1, 0, 0, 1, 0, 1, 1, 0]
+    m = np.zeros((ncz, ncy, ncx, 3))
+    m[..., 2] = 1.0
+    for b in range(len(pat1)):
+        m[:, 0:4, b * L:(b + 1) * L, 2] = -1.0 if pat1[b] else 1.0
+        m[:, 6:10, b * L:(b + 1) * L, 2] = -1.0 if pat2[b] else 1.0
+    m = m.reshape(-1, 3)
+    O = o.MsOracle(p1)
+    O.set_cells(m)
+    O.set_window(o.ms_target(p1, 0.0))
+    O.run(240, follow=True)
+    assert O.window == o.ms_target(p1, 240e-16) > 15
+    t1 = O.step * 1e-16
+    p2 = o.MsParams(ncx, ncy, ncz, cell, r, wx, x0=3.2 * cell - v * t1, y0=8 * cell, **kw)
+    O.set_drivers(p2)
+    O.set_window(o.ms_target(p2, t1))
+    assert O.window == o.ms_target(p1, 0.0)
+    O.run(240, follow=True)
+    assert O.window == o.ms_target(p2, O.step * 1e-16) > 15
+    assert np.array_equal(O.cells()[O.window * 0:], O.cells())
+    cells = O.cells().reshape(ncz, ncy, ncx, 3)
+    outside = np.ones(ncx, bool)
+    outside[O.window:O.window + wx] = False
+    assert np.array_equal(cells[:, :, outside], m.reshape(ncz, ncy, ncx, 3)[:, :, outside])
+    for (c0, c1), pat in (((0, 4), pat1), ((6, 10), pat2)):
+        sig, bits = O.read_track(0.0, L * cell, len(pat), c0, c1)
+        assert list(bits) == pat
+        assert np.array_equal(np.abs(sig), np.ones(len(pat)))
+    S = O.moments()
+    assert np.array_equal(np.abs(S[:, 2]), np.ones(len(S))) and not S[:, :2].any()
+
+
+def check_window_replacement_hands_back():
+    """Placing a window elsewhere first hands the old window's sites back to their cells by
+    Eq. 6 (brute force over each cell's sites), as the trailing column of a move is; after
+    set_cells the old sites are stale, and a re-placement hands nothing back."""
+    ncx, ncy, ncz, r, wx = 12, 2, 1, 2, 4
+    p = o.MsParams(ncx, ncy, ncz, 2 * A, r, wx, J=J_SC, ku=KU, dt=1e-16, T_amb=200.0, seed=3)
+    O = o.MsOracle(p)
+    m0 = _tilted(p.n_cells, 4, 50.0)
+    O.set_cells(m0)
+    O.set_window(2)
+    S = _tilted(O.nw, 5, 70.0)
+    O.set_moments(S)
+    O.set_window(7)
+    cells = O.cells().reshape(ncz, ncy, ncx, 3)
+    Sw = S.reshape(ncz * r, ncy * r, wx * r, 3)
+    for cy in range(ncy):
+        for cx in range(2, 2 + wx):
+            s = Sw[:, cy * r:(cy + 1) * r, (cx - 2) * r:(cx - 1) * r].reshape(-1, 3).sum(axis=0)
+            assert np.abs(cells[0, cy, cx] - s / np.linalg.norm(s)).max() < 1e-14
+    rest = np.ones(ncx, bool)
+    rest[2:2 + wx] = False
+    assert np.array_equal(cells[:, :, rest], m0.reshape(ncz, ncy, ncx, 3)[:, :, rest])
+    O.set_cells(m0)
+    O.set_window(1)
+    assert np.array_equal(O.cells(), m0)
+
+
 FAST_CHECKS = [
     check_langevin_branches, check_me_limits, check_micromagnetic_damping_law,
     check_theta_max_printed_values, check_cone_distribution, check_eq6_average_brute_force,
@@ -521,5 +618,6 @@ FAST_CHECKS = [
     check_ratio_one_window_matches_atomistic_lattice, check_full_window_equals_atomistic_oracle,
     check_shift_moves_spins, check_window_target, check_read_track, check_head_profile_shape,
     check_isolated_cell_and_site_in_head_profile, check_demag_tensor_limits, check_demag_uniform_film,
-    check_demag_in_coupled_step,
+    check_demag_in_coupled_step, check_set_drivers_continues_run, check_second_pass_keeps_written_tracks,
+    check_window_replacement_hands_back,
 ]

@@ -61,6 +61,10 @@ MUTANTS = [
      "B[2] = ex[2] / p->mu_s + 2.0 * p->ku / p->mu_s * Si[2] + Bapp[2] + Bth[3 * s + 2];"),
     ("cells miss the demagnetising field", "double B[3] = {cex * lap[0] + Bapp[0] + bd[0],",
      "double B[3] = {cex * lap[0] + Bapp[0],"),
+    ("re-placed window keeps its cells", "    if (c->live) average_cells(c, c->ox, c->ox + c->p.wx);\n", ""),
+    ("new drivers ignored", "    c->p = *p;\n    c->p.drv.bits = bits;", "    c->p.drv.bits = bits;"),
+    ("new drivers reset the step count", "    c->p = *p;\n    c->p.drv.bits = bits;",
+     "    c->p = *p;\n    c->p.drv.bits = bits;\n    c->step = 0;"),
 ]
 
 
