@@ -118,7 +118,10 @@ __device__ __forceinline__ void langevin2(double x, double &L, double &Lp) {
 // replaced by bisection.  A Newton step below 1e-13 (1 + m) is taken as converged (the
 // iteration is quadratic there; the bound is absolute for small m, where coth x - 1/x loses
 // digits to cancellation and the residual is only known to about 1e-14), before the bracket
-// test, which a converged step can fail by rounding.
+// test, which a converged step can fail by rounding, but only where the root is stable
+// (slope a L' - 1 < 0).  The largest root always is; below T_C without a field, m = 0 is an
+// unstable root that a start near 0 (a cell that was above T_C) would otherwise keep.  From
+// there the Newton step stays at 0 and leaves the bracket, so bisection takes over.
 __device__ double me_root(double T_C, double T, double mu_kB, double B, double m0) {
     if (!(T > 0.0)) return 1.0;
     const double iT = 1.0 / T;
@@ -134,7 +137,7 @@ __device__ double me_root(double T_C, double T, double mu_kB, double B, double m
             hi = m;
         const double gp = a * Lp - 1.0;
         const double mn = m - g / gp;
-        if (fabs(mn - m) <= 1e-13 * (1.0 + m)) return mn;
+        if (fabs(mn - m) <= 1e-13 * (1.0 + m) && gp < 0.0) return mn;
         m = (mn > lo && mn < hi) ? mn : 0.5 * (lo + hi);
         if (hi - lo <= 1e-16 * hi) return lo;
     }
@@ -713,6 +716,7 @@ struct hamr_ms_ctx {
     long long step = 0;
     long long events = 0;         // thermalisation events so far
     bool grains_set = false, cells_set = false;
+    bool window_live = false;     // the window's sites are newer than its cells (placed, cells not replaced since)
     // demagnetising field (Eq. 7): padded grid, tensor spectra [6][Pc], work arrays, plans
     bool demag = false;
     Pad pad{};
@@ -1281,6 +1285,7 @@ int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], cons
         return msfail(h, HAMR_ERR_ARG, "bad bit sequence (bits, bit_len > 0, ramp_len >= 0)");
     MsDeviceGuard dg(h->device);
     ReplicaDev &D = h->D;
+    h->Bm_last = NAN;  // the field law changed: no column keeps its last m_e solve
     D.B0 = B0;
     for (int k = 0; k < 3; ++k) D.dir[k] = dir[k];
     D.n_bits = n_bits;
@@ -1302,10 +1307,13 @@ int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, doub
     if (!h) return HAMR_ERR_ARG;
     if (!(wz > 0)) {
         h->P.profile = 0;
+        // every column's m_e was solved with its own profile field: solve them all again
+        h->Bm_last = NAN;
         return HAMR_OK;
     }
     if (!isfinite(Bx0) || !isfinite(wz) || !isfinite(dz) || !(wx > 0) || !isfinite(wx) || !isfinite(dx))
         return msfail(h, HAMR_ERR_ARG, "head profile: finite values, widths > 0");
+    h->Bm_last = NAN;
     h->P.profile = 1;
     h->P.pBx0 = Bx0;
     h->P.pwz = wz;
@@ -1341,6 +1349,7 @@ int hamr_ms_set_cells(hamr_ms_t h, const double *m) {
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     h->cells_set = true;
+    h->window_live = false;
     return HAMR_OK;
 }
 
@@ -1351,6 +1360,13 @@ int hamr_ms_set_window(hamr_ms_t h, int32_t x0_cells) {
                       h->P.ncx);
     if (!h->cells_set) return msfail(h, HAMR_ERR_STATE, "set the cells (hamr_ms_set_cells) before the window");
     MsDeviceGuard dg(h->device);
+    // a window already placed hands its sites back to its cells by Eq. 6 first (as the trailing
+    // column of a move does), unless the cells have been replaced since
+    if (h->ox >= 0 && h->window_live) {
+        int rc = h->prec == HAMR_FP64 ? ms_average<double>(h, h->ox, h->P.wx) : ms_average<float>(h, h->ox, h->P.wx);
+        if (rc) return rc;
+    }
+    h->window_live = true;
     h->ox = x0_cells;
     const double t = (double)h->step * h->P.dt;
     int rc = h->prec == HAMR_FP64 ? ms_thermalise<double>(h, h->ox, h->ox + h->P.wx, t)

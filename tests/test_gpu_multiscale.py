@@ -36,6 +36,16 @@ def pair(w, precision="fp64", profile=None, demag=False):
     return p, O, G
 
 
+def params(w, T=None, F=None, profile=None, demag=False):
+    """Oracle parameters of an input description with the drivers T, F (those of w by default)."""
+    T, F = T or w["T"], F or w["field"]
+    return orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                        ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
+                        seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
+                        bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"],
+                        profile=profile, demag=demag)
+
+
 def tilted_cells(w, seed=3, deg=35.0):
     n = w["ncx"] * w["ncy"] * w["ncz"]
     S = I.initial_state(n, "tilt", seed=seed, tilt_deg=deg)
@@ -233,3 +243,94 @@ def test_call_order_and_arguments():
             with pytest.raises(HamrError) as e:
                 G.read_track(*args)
             assert e.value.code == ERR_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_head_profile_switched_off_mid_run(prec):
+    """After the head profile is switched off, every column's m_e(T) is solved again with the
+    uniform field: no column keeps an m_e from its profile field, including those far from the
+    spot whose temperature has not changed (steps after the switch against the oracle)."""
+    w = I.multiscale_track(ncx=40, ncy=6, ncz=2, cell=1e-9, ratio=2, wx=8, grain_d=5e-9, seed=28, v=1.2e5,
+                           x_spot=12.013e-9)
+    w["field"].update(bit_len=4e-9, ramp_len=0.5e-9, head_x0=12.4e-9, head_v=1.2e5, B0=1.5)
+    prof = dict(Bx0=0.6, wz=3e-9, dz=1e-9, wx=2e-9, dx=-1e-9)
+    p, O, G = pair(w, prec, profile=prof)
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        O.run(60, follow=True)
+        G.steps(60, follow=True)
+        G.set_head_profile(wz=0.0)
+        O.set_drivers(params(w))
+        O.run(80, follow=True)
+        G.steps(80, follow=True)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], (dm, dS)
+        assert G.window()[0] == O.window
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_zero_field_columns_cool_through_tc(prec):
+    """No write field: the passing spot heats columns above T_C (m_e = 0) and they cool below it
+    again, where m_e(T) must return to the largest root of the mean-field equation, not stay at
+    the unstable root 0 its last solve started from (against the oracle's bisection)."""
+    w = I.multiscale_track(ncx=30, ncy=4, ncz=2, cell=1e-9, ratio=2, wx=6, grain_d=5e-9, seed=29, v=4e5,
+                           x_spot=7.013e-9)
+    w["T"].update(T_peak=1500.0, fwhm=6e-9)
+    w["field"].update(B0=0.0)
+    p, O, G = pair(w, prec)
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        ox = O.window
+        for block in (150, 150):
+            O.run(block, follow=True)
+            G.steps(block, follow=True)
+            dm, dS = compare(O, G)
+            assert dm < TOL[prec] and dS < TOL[prec], (block, dm, dS)
+        assert O.window >= ox + 8
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_parallel_track_second_pass_matches_oracle(prec):
+    """Two tracks written side by side (Sec. III): a first pass with the spot and the head over
+    one row band, then a second pass with the spot centre moved across the track by 15 nm
+    scaled to this mesh (new temperature profile, spot and head restarted at the current time,
+    the window placed back at the new spot, handing the old one back by Eq. 6).  Cells and
+    window spins against the oracle after each pass, and both bands read back the same."""
+    dt, v = 1e-16, 2e5
+    w = I.multiscale_track(ncx=40, ncy=16, ncz=2, cell=1e-9, ratio=2, wx=8, grain_d=5e-9, seed=30, v=v,
+                           x_spot=8.013e-9)
+    w["T"].update(y0=4.5e-9, fwhm=6e-9, T_peak=1100.0)
+    w["field"].update(bit_len=4e-9, ramp_len=0.5e-9, head_x0=8.4e-9, head_v=v, B0=2.0)
+    p, O, G = pair(w, prec)
+    n1 = 120
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        O.run(n1, follow=True)
+        G.steps(n1, follow=True)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], ("first pass", dm, dS)
+        t1 = n1 * dt
+        T2 = dict(w["T"], x0=w["T"]["x0"] - v * t1, y0=11.5e-9)
+        F2 = dict(w["field"], head_x0=w["field"]["head_x0"] - v * t1, bits=I.bits_of("1011001"))
+        G.set_temperature_profile(**T2)
+        G.set_field_sequence(**F2)
+        p2 = params(w, T2, F2)
+        O.set_drivers(p2)
+        ox2 = orc.ms_target(p2, t1)
+        assert ox2 < O.window
+        O.set_window(ox2)
+        G.set_window(ox2)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], ("re-placed", dm, dS)
+        O.run(n1, follow=True)
+        G.steps(n1, follow=True)
+        dm, dS = compare(O, G)
+        assert dm < TOL[prec] and dS < TOL[prec], ("second pass", dm, dS)
+        assert G.window()[0] == O.window
+        for band in ((0, 8), (8, 16)):
+            sig, bits = G.read_track(0.0, 4e-9, 9, *band)
+            osig, obits = O.read_track(0.0, 4e-9, 9, *band)
+            assert np.abs(sig - osig).max() < TOL[prec]
