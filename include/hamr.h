@@ -215,6 +215,14 @@ int hamr_load_state(hamr_t h, const char *path);
  * Errors: ARG (shape not compiled), STATE, CUDA. */
 int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged);
 int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged);
+/* Planes per work item of the fused FP32 kernel.  A column block spans all planes of its
+ * replica unless the batch has too few blocks to keep every resident CTA busy; then each
+ * block is also split into ranges of at most `planes` planes (at least 4, chosen by a work
+ * model that weighs the resident CTAs against the two recomputed halo planes per range).  The
+ * results do not depend on the split: the S' of a range's boundary planes is recomputed with
+ * the same noise.  planes = 0 (the default): chosen by the work model; > 0: fixed.
+ * hamr_query key 6 reports the length in use, key 5 the number of work items.  Errors: ARG. */
+int hamr_set_plane_range(hamr_t h, int32_t planes);
 int hamr_autotune(hamr_t h, int32_t steps_per_trial);
 
 /* Failure-detection test hook (no counterpart in the paper).  The next step call makes the
@@ -226,7 +234,8 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial);
 int hamr_inject_wait_timeout(hamr_t h, int32_t polls);
 
 /* Sizes: key 0 = total lattice sites, 1 = magnetic sites, 2 = device bytes held,
- * 3 = kernel launches per step (excluding records), 4 = storage slots. */
+ * 3 = kernel launches per step (excluding records), 4 = storage slots, 5 = work items of the
+ * fused FP32 kernel, 6 = its planes per work item (5 and 6 build the work list if needed). */
 int hamr_query(hamr_t h, int32_t key, int64_t *value);
 
 /* ---- One step without allocation ------------------------------------------------------
@@ -361,7 +370,12 @@ int hamr_ms_set_demag(hamr_ms_t h, int32_t on);
  * set to 0).  ARG on non-finite values. */
 int hamr_ms_set_cells(hamr_ms_t h, const double *m);
 /* Places the window at cell column x0_cells and thermalises all of it from the cells (one
- * thermalisation event).  ARG if the window leaves the track, STATE before set_cells. */
+ * thermalisation event).  A window already placed first hands its sites back to its cells by
+ * Eq. 6, as the trailing column does when the window moves (Sec. II), unless set_cells has
+ * replaced the cells since.  A second pass along a parallel track (Sec. III) is a new spot
+ * centre y0 (set_temperature_profile), spot and head starting points for the current time
+ * (set_temperature_profile, set_field_sequence) and this call at the new spot.
+ * ARG if the window leaves the track, STATE before set_cells. */
 int hamr_ms_set_window(hamr_ms_t h, int32_t x0_cells);
 /* Overwrites the window's spins (3 nxw nyw nzw doubles, AoS; copied).  STATE before the
  * window is placed. */

@@ -504,11 +504,38 @@ int build_items(hamr_t h) {
                 mixed.reserve(inner.size() + halo.size());
                 for (uint16_t p : inner) mixed.push_back((uint16_t)(p | 0x8000u));
                 mixed.insert(mixed.end(), halo.begin(), halo.end());
+                w.zr = 0;
                 items.push_back(w);
                 lists.push_back(std::move(mixed));
                 cost.push_back((long long)(2 * (w.counts & 0xffff) + (w.counts >> 16) + 64) * (R.nz + 2));
             }
     }
+    // Plane ranges.  A batch whose column blocks are too few to keep the resident CTAs busy is
+    // also split along z.  Modelled time of a launch: the larger of the total work over the
+    // resident CTAs and the longest item, an item of L planes of a block costing that block's
+    // work per plane times L + 4 (its march runs L + 2 steps, the prologue about 2 more).  The
+    // range length with the least modelled time wins; a shorter one must gain 5 %.
+    const int bps = std::max(1, fused_max_blocks_per_sm(h->variant, tetragonal(h)));
+    const double slots = (double)bps * std::max(1, h->num_sms);
+    int maxnz = 1;
+    for (const ReplicaDev &R : h->reps_h) maxnz = std::max(maxnz, R.nz);
+    int Lz = maxnz;
+    double best = 1e300;
+    for (int L = maxnz; L >= std::min(4, maxnz); --L) {
+        double total = 0.0, longest = 0.0;
+        for (size_t i = 0; i < items.size(); ++i) {
+            const int nz = h->reps_h[items[i].r].nz, nr = (nz + L - 1) / L;
+            const double wp = (double)cost[i] / (nz + 2);
+            total += wp * (nz + 4.0 * nr);
+            longest = std::max(longest, wp * ((nz + nr - 1) / nr + 4));
+        }
+        const double c = std::max(total / slots, longest);
+        if (c < 0.95 * best) {
+            best = c;
+            Lz = L;
+        }
+    }
+    if (h->z_range_set > 0) Lz = h->z_range_set;
     // replicas by decreasing total cost, the blocks of a replica together and in row order:
     // neighbouring blocks then run at the same time and share their halo planes through L2
     std::vector<long long> rcost(h->R, 0);
@@ -520,12 +547,19 @@ int build_items(hamr_t h) {
         if (ra != rb) return rcost[ra] != rcost[rb] ? rcost[ra] > rcost[rb] : ra < rb;
         return a < b;
     });
-    std::vector<WorkItem> sorted(items.size());
+    // each block once per plane range, its ranges in a row (they share the block's column list)
+    std::vector<WorkItem> sorted;
     std::vector<uint16_t> flat;
     for (size_t i = 0; i < idx.size(); ++i) {
-        sorted[i] = items[idx[i]];
-        sorted[i].list_off = (int)flat.size();
+        WorkItem w = items[idx[i]];
+        w.list_off = (int)flat.size();
         flat.insert(flat.end(), lists[idx[i]].begin(), lists[idx[i]].end());
+        const int nz = h->reps_h[w.r].nz, nr = (nz + Lz - 1) / Lz;
+        for (int j = 0; j < nr; ++j) {
+            const int za = (int)((long long)j * nz / nr), zb = (int)((long long)(j + 1) * nz / nr);
+            w.zr = za | ((zb - za) << 16);
+            sorted.push_back(w);
+        }
     }
     if (sorted.size() > (size_t)h->items_cap) {
         dfree(h->items_d);
@@ -548,7 +582,8 @@ int build_items(hamr_t h) {
                           h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->n_items = (int)sorted.size();
-    const int bps = std::max(1, fused_max_blocks_per_sm(h->variant, tetragonal(h)));
+    h->z_range = Lz;
+    h->z_split = Lz < maxnz;
     h->fused_grid = std::max(1, std::min(h->n_items, bps * h->num_sms));
     h->items_dirty = false;
     clear_graphs(h);
@@ -585,7 +620,7 @@ int enqueue_block(hamr_t h, int G, bool record) {
         a.Sbuf1 = (float *)h->S[1];
         for (int i = 0; i < G; ++i) {
             a.step_off = i;
-            CK(h, launch_fused_step(h->variant, tetragonal(h), a, h->fused_grid, h->stream));
+            CK(h, launch_fused_step(h->variant, tetragonal(h), h->z_split, a, h->fused_grid, h->stream));
         }
         if (record)
             CK(h, launch_grain_sums_fx(a.Sbuf0, a.Sbuf1, h->NS, h->runs_d, h->gitems_d, h->n_gitems, h->ctl_d, G,
@@ -1376,6 +1411,17 @@ int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged) {
     return HAMR_OK;
 }
 
+int hamr_set_plane_range(hamr_t h, int32_t planes) {
+    if (!h) return HAMR_ERR_ARG;
+    if (planes < 0) return fail(h, HAMR_ERR_ARG, "planes must be >= 0");
+    if (planes != h->z_range_set) {
+        h->z_range_set = planes;
+        h->items_dirty = true;
+        clear_graphs(h);
+    }
+    return HAMR_OK;
+}
+
 int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     if (!h) return HAMR_ERR_ARG;
     Range nv("hamr autotune");
@@ -1448,6 +1494,16 @@ int hamr_query(hamr_t h, int32_t key, int64_t *value) {
         case 4:
             *value = h->NS;
             return HAMR_OK;
+        case 5:
+        case 6: {
+            if (fused_mode(h) && h->items_dirty) {
+                DeviceGuard dg(h->device);
+                int rc = build_items(h);
+                if (rc) return rc;
+            }
+            *value = key == 5 ? h->n_items : h->z_range;
+            return HAMR_OK;
+        }
         default:
             return fail(h, HAMR_ERR_ARG, "unknown query key %d", key);
     }

@@ -82,6 +82,7 @@ struct WorkItem {
     int list_off;  // first entry of its column list
     int counts;    // listed columns | interior columns << 16
     int stage;     // 1: staged by TMA | columns between the staged origin and x0 - 2, << 8
+    int zr;        // first plane | planes << 16
 };
 
 // A compiled variant of the fused kernel.
@@ -131,8 +132,9 @@ struct FusedArgs {
 
 // kernel launchers (kernels_*.cu)
 cudaError_t launch_plain_step(int prec, const void *args, int n_blocks, bool record, cudaStream_t st);
-// tet: the L1_0 (tetragonal three-shell) stencil instead of the simple-cubic one
-cudaError_t launch_fused_step(int variant, bool tet, const FusedArgs &a, int grid, cudaStream_t st);
+// tet: the L1_0 (tetragonal three-shell) stencil instead of the simple-cubic one; zr: some work
+// items cover plane ranges (WorkItem::zr)
+cudaError_t launch_fused_step(int variant, bool tet, bool zr, const FusedArgs &a, int grid, cudaStream_t st);
 // exact per-grain sums (fixed point, 2^-24) of the FP32 state after G steps from ctl->step,
 // into grain_fx (read by k_bookkeeping at a record point)
 cudaError_t launch_grain_sums_fx(const float *S0, const float *S1, long long NS, const unsigned long long *runs,
@@ -226,6 +228,9 @@ struct hamr_ctx {
     CUtensorMap *maps_d = nullptr;    // [R][2] (variant-dependent box)
     std::vector<int> tma_ok;          // replica staged by TMA (open in x and y, no grain mask)
     int fused_grid = 0;
+    int z_range = 0;                  // planes per work item (the longest; 0 until items are built)
+    int z_range_set = 0;              // > 0: plane range fixed by hamr_set_plane_range
+    bool z_split = false;             // some work items cover plane ranges (the range kernel runs)
     unsigned inject_polls = 0;        // >0: the next step block runs the failure test
     bool items_dirty = true;
     // per-grain runs for the record sums of the FP32 fused path (rebuilt after grain changes)

@@ -5,9 +5,13 @@
 // plane and 4 in-plane diagonals (three shells).  Both are stencils over the same staged
 // planes: the diagonals are the corners of the halo that the nearest neighbours need anyway.
 //
-// Work item = a block of bx x by columns of one replica spanning all nz planes.  The CTA
-// stages, plane by plane, the spins of the block plus a two-column halo in shared memory and
-// marches up the planes.  Staging runs three planes ahead of the march through a four-slot
+// Work item = a block of bx x by columns of one replica over a range of planes [z0, z0 + nzl)
+// (all nz planes unless a lattice has too few column blocks to fill the GPU).  The CTA stages,
+// plane by plane, the spins of the block plus a two-column halo in shared memory and marches
+// up the planes, from the plane below its range to the plane above it: the predictor on those
+// two planes recomputes the S' that the neighbouring ranges compute (the same noise, as the
+// counter is the site), so the corrector never needs another CTA's S'.  Planes are numbered
+// from z0 within the item (local k = z - z0).  Staging runs three planes ahead of the march through a four-slot
 // ring with one mbarrier per slot: one thread (the waiter) issues a TMA tile copy of the
 // three spin components (zero-filled beyond open edges), arriving once for the whole CTA;
 // replicas whose blocks wrap around a periodic edge, or whose grains touch, are staged instead
@@ -258,7 +262,9 @@ __device__ __forceinline__ float3 field_p(const FusedArgs &a, float3 h, const fl
                        fmaf(a.cJ[0], nn.z, fmaf(a.cJ[1], zz.z, fmaf(a.cJ[2], dg.z, h.z))));
 }
 
-template <bool TET, int NT, int E, int SW, int SH, int MINB>
+// ZR: the work items cover plane ranges (false: every item spans all planes of its replica,
+// and the range arithmetic compiles away)
+template <bool TET, int NT, int E, int SW, int SH, int MINB, bool ZR>
 __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
     using Sh = FusedShape<NT, SW, SH>;
     constexpr int CAPS = Sh::CAPS, LPT = Sh::LPT, SLOT_F = Sh::SLOT_F;
@@ -302,6 +308,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         const WorkItem W = a.items[it];
         const ReplicaDev &R = a.reps[W.r];
         const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px;
+        const int z0 = ZR ? W.zr & 0xffff : 0, nzl = ZR ? W.zr >> 16 : nz;  // the item's planes [z0, z0 + nzl)
         const int off = (int)R.off;
         const int plane = px * ny;
         const int bx = W.bxy & 0xffff, by = W.bxy >> 16;
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         int c[E];               // staged-region position
         float sig[E];           // thermal-field scale of the column
         unsigned scol[E];       // site index of the column on plane 0
-        int ocol[E];            // storage slot of the column on plane 0
+        int ocol[E];            // storage slot of the column on the item's first plane z0
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             act[j] = tid + j * NT < n_act;
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
                 const float T = temperature_f(R, (wx + 0.5f) * a.ax, (wy + 0.5f) * a.ay, t);
                 sig[j] = a.sig0 * sqrtf(T);
                 scol[j] = (unsigned)wx + (unsigned)nx * (unsigned)wy;
-                ocol[j] = off + wx + px * wy;
+                ocol[j] = off + wx + px * (wy + ny * z0);  // the column's slot on plane z0
             }
         }
         // Only the warps that hold list entries march; the others wait at the end of the item.
@@ -373,13 +380,13 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
         // stage, issues the TMA fills and waits for them (the waiter).
         const int nmarch = tma ? min(NT, (n_act + 31) & ~31) : NT;
         const int waiter = nmarch - 32;
-        // stage plane p into ring slot p mod 4 (planes beyond nz + 1 are never needed)
+        // stage local plane p into ring slot p mod 4 (planes beyond nzl + 1 are never needed)
         auto issue = [&](int p, bool withhold = false) {
-            if (p > nz + 1) return;
+            if (p > nzl + 1) return;
             const int slot = (p + 4) & 3;
             float *dst = sS + slot * SLOT_F;
             bool ok = true;
-            const int z = wrap_coord(p, nz, a.per[2], ok);
+            const int z = wrap_coord(z0 + p, nz, a.per[2], ok);
             // failure-detection test: the phase of this fill can then never complete
             if (withhold && tid == waiter) return;
             if (tid == waiter) s_hi_issued = p;
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
             constexpr int SK = (PH + 3) & 3, SK1 = PH & 3, SKM1 = (PH + 2) & 3, SKM2 = (PH + 1) & 3;
             issue(k + 3);  // into slot (k + 3) mod 4 = SKM1, left by plane k-1 (kept in registers)
             bool zok = true;
-            const int wz = wrap_coord(k, nz, a.per[2], zok);
+            const int wz = wrap_coord(z0 + k, nz, a.per[2], zok);
             float4 sp[E];       // S' of plane k (own, for the corrector's z+ neighbour)
             float ppx[E], ppy[E], ppz[E];
             unsigned g0[E];
@@ -539,11 +546,11 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
             }
             // plane k+2 (read by the next step's predictor) is awaited by thread 0 before the
             // step's one barrier, which also carries the failure vote
-            if (tid == waiter && k + 2 <= nz + 1) await(k + 2);
+            if (tid == waiter && k + 2 <= nzl + 1) await(k + 2);
             stop = bar_or(1, nmarch, bad);
             // ---- corrector on plane k-1 from S' planes k-2 (slot SKM2), k-1 (SKM1) and k (own, sp)
             const int kc = k - 1;
-            if (kc >= 0 && kc < nz) {
+            if (kc >= 0 && kc < nzl) {
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
                     if (!inner[j]) continue;
@@ -606,12 +613,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
             }
         };
 
-        // k runs from -1 to nz; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
-        for (int kb = -1; kb <= nz && !stop; kb += 4) {
+        // k runs from -1 to nzl; k = kb + PH with kb = -1 (mod 4), so plane k sits in slot (PH + 3) % 4
+        for (int kb = -1; kb <= nzl && !stop; kb += 4) {
             march(IC<0>(), kb);
-            if (!stop && kb + 1 <= nz) march(IC<1>(), kb + 1);
-            if (!stop && kb + 2 <= nz) march(IC<2>(), kb + 2);
-            if (!stop && kb + 3 <= nz) march(IC<3>(), kb + 3);
+            if (!stop && kb + 1 <= nzl) march(IC<1>(), kb + 1);
+            if (!stop && kb + 2 <= nzl) march(IC<2>(), kb + 2);
+            if (!stop && kb + 3 <= nzl) march(IC<3>(), kb + 3);
         }
         if (stop) {
             // give the fills issued after the last awaited plane a bounded time to land before
@@ -632,12 +639,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(FusedArgs a) {
 
 // Opt in to the variant's dynamic shared memory (done before any stream capture, when the
 // work list is built).
-template <bool TET, int NT, int E, int SW, int SH, int MINB>
+template <bool TET, int NT, int E, int SW, int SH, int MINB, bool ZR>
 static cudaError_t ensure_attrs() {
     using Sh = FusedShape<NT, SW, SH>;
     static bool init = false;
     if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<TET, NT, E, SW, SH, MINB, ZR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
         if (e != cudaSuccess) return e;
         init = true;
@@ -646,23 +653,30 @@ static cudaError_t ensure_attrs() {
 }
 
 template <bool TET, int NT, int E, int SW, int SH, int MINB>
-static cudaError_t launch_variant(const FusedArgs &a, int grid, cudaStream_t st) {
+static cudaError_t launch_variant(const FusedArgs &a, bool zr, int grid, cudaStream_t st) {
     using Sh = FusedShape<NT, SW, SH>;
-    cudaError_t e = ensure_attrs<TET, NT, E, SW, SH, MINB>();
+    cudaError_t e = zr ? ensure_attrs<TET, NT, E, SW, SH, MINB, true>() : ensure_attrs<TET, NT, E, SW, SH, MINB, false>();
     if (e != cudaSuccess) return e;
-    k_fused<TET, NT, E, SW, SH, MINB><<<grid, NT, Sh::smem, st>>>(a);
+    if (zr)
+        k_fused<TET, NT, E, SW, SH, MINB, true><<<grid, NT, Sh::smem, st>>>(a);
+    else
+        k_fused<TET, NT, E, SW, SH, MINB, false><<<grid, NT, Sh::smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <bool TET, int NT, int E, int SW, int SH, int MINB>
 static int blocks_per_sm() {
     using Sh = FusedShape<NT, SW, SH>;
-    int n = 0;
-    if (ensure_attrs<TET, NT, E, SW, SH, MINB>() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<TET, NT, E, SW, SH, MINB>, NT, Sh::smem) !=
-        cudaSuccess)
+    int n = 0, m = 0;
+    if (ensure_attrs<TET, NT, E, SW, SH, MINB, false>() != cudaSuccess ||
+        ensure_attrs<TET, NT, E, SW, SH, MINB, true>() != cudaSuccess)
         return 0;
-    return n;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<TET, NT, E, SW, SH, MINB, false>, NT, Sh::smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_fused<TET, NT, E, SW, SH, MINB, true>, NT, Sh::smem) !=
+            cudaSuccess)
+        return 0;
+    return n < m ? n : m;
 }
 
 // compiled variants: threads per CTA, listed columns per thread, the staged region's pitch x
@@ -674,9 +688,9 @@ static int blocks_per_sm() {
     X(0, 512, 1, 36, 24, 2) X(1, 1024, 1, 68, 24, 1) X(2, 256, 1, 36, 14, 3) X(3, 256, 2, 36, 24, 2)
 
 template <bool TET>
-cudaError_t launch_fused_lattice(int v, const FusedArgs &a, int grid, cudaStream_t st) {
+cudaError_t launch_fused_lattice(int v, bool zr, const FusedArgs &a, int grid, cudaStream_t st) {
 #define X(I, NT, E, SW, SH, MINB) \
-    if (v == I) return launch_variant<TET, NT, E, SW, SH, MINB>(a, grid, st);
+    if (v == I) return launch_variant<TET, NT, E, SW, SH, MINB>(a, zr, grid, st);
     HAMR_FUSED_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -3,7 +3,7 @@
 
 namespace hamr {
 
-template cudaError_t launch_fused_lattice<true>(int, const FusedArgs &, int, cudaStream_t);
+template cudaError_t launch_fused_lattice<true>(int, bool, const FusedArgs &, int, cudaStream_t);
 template int fused_blocks_lattice<true>(int);
 
 }  // namespace hamr

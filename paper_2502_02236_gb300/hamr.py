@@ -25,7 +25,7 @@ EXPORTS = [
     "hamr_synchronize", "hamr_read_moments", "hamr_read_moments_device",
     "hamr_read_magnetisation", "hamr_clear_records", "hamr_read_energy", "hamr_get_step",
     "hamr_set_step", "hamr_check_finite", "hamr_save_state", "hamr_load_state", "hamr_set_tile",
-    "hamr_get_tile", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
+    "hamr_get_tile", "hamr_set_plane_range", "hamr_autotune", "hamr_query", "hamr_last_error", "hamr_destroy",
     "hamr_sllg_heun_step_noalloc", "hamr_inject_wait_timeout",
     "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
     "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
@@ -116,6 +116,7 @@ def lib():
             "hamr_load_state": [vp, ctypes.c_char_p],
             "hamr_set_tile": [vp, i32, i32],
             "hamr_get_tile": [vp, vp, vp],
+            "hamr_set_plane_range": [vp, i32],
             "hamr_autotune": [vp, i32],
             "hamr_query": [vp, i32, vp],
             "hamr_sllg_heun_step_noalloc": [vp, vp, vp, vp, i64, vp],
@@ -346,6 +347,10 @@ class Lattice:
         a, b = ctypes.c_int32(), ctypes.c_int32()
         self._ck(lib().hamr_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def set_plane_range(self, planes):
+        """Planes per work item of the fused FP32 kernel (0: chosen by the work model)."""
+        self._ck(lib().hamr_set_plane_range(self._h, int(planes)))
 
     def autotune(self, steps_per_trial=20):
         self._ck(lib().hamr_autotune(self._h, int(steps_per_trial)))

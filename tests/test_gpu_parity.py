@@ -127,6 +127,43 @@ def test_fp32_granular_drivers_every_tile(tile):
     assert max_abs(Mg, Mo) < TOL32
 
 
+@pytest.mark.parametrize("lattice,periodic", [("sc", (False, False, False)), ("sc", (True, False, True)),
+                                              ("l10", (False, False, True)), ("l10", (False, True, False))])
+def test_plane_ranges_bitwise_equal_to_whole_columns(lattice, periodic):
+    """Work items over plane ranges (the split used when a batch has too few column blocks for
+    the GPU) give bitwise the spins and records of whole-column items: the predictor on a
+    range's boundary planes recomputes the neighbouring range's S' with the same noise.  The
+    work model splits this small batch by itself."""
+    reps = [tiny_track(45, 37, 13, seed=5), tiny_track(23, 30, 9, seed=7),
+            dict(dims=(40, 30, 7), seed=8, init="random", T=dict(T_amb=700.0), field=dict(B0=0.8, direction=(0, 0, -1)))]
+    if lattice == "sc":
+        w = workload_of(reps, periodic=periodic)
+    else:
+        w = dict(lattice="l10", precision="fp32", neighbours="stencil", a=0.385e-9, c=0.371e-9, periodic=periodic,
+                 mu_s=I.MU_S, ku=I.KU_L10, alpha=0.1, dt=1e-16, J=[I.J_SC, 0.5 * I.J_SC, 0.1 * I.J_SC], replicas=reps)
+    S0 = [initial(rep) for rep in reps]
+    got = {}
+    for planes in (0, 13, 4, 5):
+        lat = gpu_lattice(w, S0=S0)
+        lat.set_plane_range(planes)
+        used = lat.query(6)
+        assert used == (planes or used) and 4 <= used <= 13, (planes, used)
+        if planes == 0:
+            assert used < 13 and lat.query(5) > 2 * 3   # split by the work model
+        lat.sllg_heun_steps(41, 20)
+        got[planes] = ([lat.read_moments(r) for r in range(len(reps))],
+                       [lat.read_magnetisation(r)[0] for r in range(len(reps))])
+        lat.close()
+    for planes in (0, 4, 5):
+        for r in range(len(reps)):
+            assert np.array_equal(got[planes][0][r], got[13][0][r]), (planes, r)
+            assert np.array_equal(got[planes][1][r], got[13][1][r]), (planes, r)
+    o = oracle_for(w, 1)
+    S = S0[1].copy()
+    o.run(S, 0, 41, 0)
+    assert max_abs(got[0][0][1], S) < TOL32
+
+
 def uneven_replicas():
     """Uneven batch: a single spin, thin slabs, a ragged granular piece, a replica with no
     magnetic site, and one with adjacent different grains (bonds that must be cut)."""
