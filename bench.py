@@ -168,18 +168,54 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def kernel_traffic():
-    """DRAM bytes per fused launch from the committed ncu summary, if it was taken on the
-    kernel sources as they are now (else None)."""
+def kernel_counters():
+    """DRAM bytes and warp instructions per fused launch from the committed ncu summary, if
+    it was taken on the kernel sources as they are now (else None)."""
     path = os.path.join(ROOT, "profiles", "fused_ensemble256_traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         if t.get("kernel_sha256") == kernel_sources_sha256():
-            return t.get("dram_bytes_per_launch")
+            return t
     except (OSError, ValueError):
         pass
     return None
+
+
+def issue_roof(warp_inst, avg_launch_ms, sm_mhz):
+    """The instruction-issue roof of a launch: its warp instructions over every SM's four
+    schedulers issuing one instruction per cycle at the sampled SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if not warp_inst or not sm_mhz:
+        return None
+    roof_ms = warp_inst / (sms * 4 * sm_mhz * 1e6) * 1e3
+    return {"warp_inst_per_launch": warp_inst, "sms": sms, "issue_per_clk": 4 * sms, "sm_mhz": sm_mhz,
+            "roof_ms": roof_ms, "frac": roof_ms / avg_launch_ms}
+
+
+def oracle_error(lat, w, reps, n_per=40):
+    """Largest |S_gpu - S_oracle| over sampled sites of the given replicas after one step of the
+    handle from its current state; the FP64 oracle steps each sampled site from the same
+    pre-step state (edges and random sites of every replica)."""
+    import oracle as orc
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from common import oracle_params
+    S0 = {r: lat.read_moments(r) for r in reps}
+    step = lat.step
+    lat.sllg_heun_steps(1, 0)
+    worst, count = 0.0, 0
+    for r in reps:
+        rep = w["replicas"][r]
+        nx, ny, nz = rep["dims"]
+        n = nx * ny * nz
+        rng = np.random.default_rng(r)
+        sites = np.unique(np.concatenate([rng.integers(0, n, size=n_per), [0, nx - 1, nx * (ny - 1), n - 1]]))
+        want = orc.step_sites(oracle_params(w, r), rep.get("grain"), S0[r], step, sites)
+        worst = max(worst, float(np.abs(lat.read_moments(r)[sites] - want).max()))
+        count += len(sites)
+    return {"max_abs_spin": worst, "sites": count, "replicas": len(reps),
+            "what": "one step from the handle's state, every sampled site against the FP64 oracle"}
 
 
 def l2_note(n_sites):
@@ -305,13 +341,17 @@ def multiscale_line(args, dist):
     m[:, 2] = 1.0
     ox = int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5))
 
-    def rate(precision, K, demag=False):
+    def make(precision):
         G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                        ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
                        seed=w["seed"] ^ (dist.rank << 48), precision=precision)
         G.set_grain_map(w["grain"])
         G.set_temperature_profile(**w["T"])
         G.set_field_sequence(**w["field"])
+        return G
+
+    def rate(precision, K, demag=False):
+        G = make(precision)
         G.set_cells(m)
         G.set_window(ox)
         if demag:
@@ -357,6 +397,17 @@ def multiscale_line(args, dist):
         el = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": nw * 2 / el, "unit": "window spin-steps/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": "2 coupled steps of the full track in %.1f s" % el}
+        # the same three coupled steps on the GPU in both precisions, against the oracle
+        for prec, key in (("fp32", None), ("fp64", "fp64")):
+            G = make(prec)
+            G.set_cells(m)
+            G.set_window(ox)
+            G.steps(3, follow=True)
+            err = {"max_abs_cell": float(np.abs(G.read_cells() - O.cells()).max()),
+                   "max_abs_spin": float(np.abs(G.read_moments() - O.moments()).max()),
+                   "what": "3 coupled steps of the full track from the same state, every cell and window spin"}
+            G.close()
+            (line[key] if key else line)["oracle_err"] = err
     return line
 
 
@@ -448,7 +499,8 @@ def main():
     t_launch = ms_k / K / 1e3
     achieved = BYTES_PER_SITE_FP32 * n_sites / t_launch / 1e9
     peak, peak_kind = peaks()
-    traffic = kernel_traffic() if args.workload == "ensemble256" else None
+    counters = kernel_counters() if args.workload == "ensemble256" and tile == (512, 864) else None
+    traffic = counters.get("dram_bytes_per_launch") if counters else None
     assert lat.check_finite()
     launches = K + K // rec
 
@@ -464,8 +516,11 @@ def main():
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic,
                         "traffic_gbs": traffic / t_launch / 1e9 if traffic else None,
+                        "frac_magnetic": BYTES_PER_SITE_FP32 * n_mag / t_launch / 1e9 / peak,
                         "peak_source": peak_kind, "kernel": "k_fused", "avg_launch_ms": t_launch * 1e3,
-                        "bytes_per_site": BYTES_PER_SITE_FP32},
+                        "bytes_per_site": BYTES_PER_SITE_FP32,
+                        "issue": issue_roof(counters.get("warp_inst_per_launch") if counters else None,
+                                            t_launch * 1e3, (clk or {}).get("sm_mhz"))},
            "clocks": clk}
 
     # plain FP64 path on the same workload (the speedup denominator)
@@ -479,7 +534,9 @@ def main():
         out["fp64_plain"] = {"value": v64, "unit": "spin-steps/s", "steps": K64, "ms_per_step": ms64 / K64,
                              "launches_per_step": 2, "dtype": "f64"}
         out["speedup_fp32_over_fp64"] = value / v64
-        lat64.close()
+        if args.no_cpu or dist.rank != 0 or dist.world != 1:
+            lat64.close()
+            lat64 = None
 
     # end to end through the C ABI with host buffers: upload all spins from pinned memory,
     # K steps with records, read the records and all spins back
@@ -510,6 +567,12 @@ def main():
         out["multiscale"] = multiscale_line(args, dist)
 
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        # the error against the FP64 oracle beside every reported rate (this leg runs the oracle)
+        chk = list(range(0, len(w["replicas"]), max(1, len(w["replicas"]) // 32)))
+        out["oracle_err"] = oracle_error(lat, w, chk)
+        if not args.no_fp64:
+            out["fp64_plain"]["oracle_err"] = oracle_error(lat64, w, chk[:8])
+            lat64.close()
         v, reps, n, steps, el = cpu_baseline(w, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": "spin-steps/s", "cores": os.cpu_count(), "kind": "oracle",
                                "sample": "FP64 oracle, replicas 0..%d of the workload (%d sites), %d steps in %.1f s"

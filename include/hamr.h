@@ -247,7 +247,8 @@ int hamr_query(hamr_t h, int32_t key, int64_t *value);
  * the FP64 path of hamr_sllg_heun_steps, a static applied field B_app and the laser spot of
  * hamr_set_temperature_profile.
  *   S_in, S_out: caller-owned device arrays of 3 n doubles (site-major, x fastest); they
- *                may be the same array.  Non-magnetic sites are copied unchanged.
+ *                are the same array or do not overlap (a partial overlap is ARG).
+ *                Non-magnetic sites are copied unchanged.
  *   grain:       caller-owned device array of n int32 grain ids (-1 = non-magnetic), or
  *                NULL for one grain.
  *   step:        the n of t_n = n dt (thermal-field counter and laser position).
@@ -258,8 +259,8 @@ int hamr_query(hamr_t h, int32_t key, int64_t *value);
  * up that array's address (cudaGetSymbolAddress) and should come before any stream capture.
  * All calls share the array and it keeps the last call's contents (nothing in it needs to
  * start at zero): calls that overlap on the GPU race.  Errors (hamr_last_error(NULL) holds
- * the message): ARG (null pointer, bad parameter, more than HAMR_NOALLOC_MAX_SITES sites),
- * CUDA. */
+ * the message): ARG (null pointer, bad parameter, more than HAMR_NOALLOC_MAX_SITES sites,
+ * S_out partly overlapping S_in), CUDA. */
 #define HAMR_NOALLOC_MAX_SITES 131072
 
 typedef struct {

@@ -172,6 +172,13 @@ extern "C" int hamr_sllg_heun_step_noalloc(const hamr_noalloc_params *p, const d
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (n > HAMR_NOALLOC_MAX_SITES)
         return reject(HAMR_ERR_ARG, "lattice has more sites than HAMR_NOALLOC_MAX_SITES (131072)");
+    {
+        // the corrector reads S_in[i] while other threads write S_out: the arrays must be the
+        // same or disjoint
+        const uintptr_t i0 = (uintptr_t)S_in, o0 = (uintptr_t)S_out, len = (uintptr_t)(3 * n) * sizeof(double);
+        if (S_out != S_in && i0 < o0 + len && o0 < i0 + len)
+            return reject(HAMR_ERR_ARG, "S_out overlaps S_in without being the same array");
+    }
     if (!(p->a > 0) || !(p->mu_s > 0) || !(p->dt > 0) || !(p->gamma > 0) || !(p->alpha >= 0) ||
         !(p->T_amb >= 0) || !(p->T_peak >= 0) || step < 0)
         return reject(HAMR_ERR_ARG, "bad physical parameter");

@@ -372,7 +372,7 @@ def sllg_heun_step_noalloc(dims, S_in, S_out, *, grain=None, step=0, periodic=(F
                            T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0, B_app=(0.0, 0.0, 0.0),
                            stream=None):
     """One FP64 Heun step through hamr_sllg_heun_step_noalloc on caller-owned device
-    tensors: S_in, S_out float64 (n, 3) (may be the same tensor), grain int32 (n,) or None.
+    tensors: S_in, S_out float64 (n, 3) (the same tensor or disjoint), grain int32 (n,) or None.
     The library allocates nothing; the call is stream-ordered on `stream` (a raw handle,
     None = the legacy default stream)."""
     p = NoallocParams()

@@ -68,6 +68,20 @@ def test_noalloc_two_steps_match_handle_path(env):
     assert np.max(np.abs(got2 - S0)) > 1e-4          # the steps did move the spins
     assert np.array_equal(got2[grain < 0], S0[grain < 0])
 
+    # and directly against the FP64 oracle for the same two steps
+    import oracle as orc
+    p = orc.sc_params(nx, ny, nz, a, I.J_SC, periodic=(True, False, False), mu_s=I.MU_S, ku=I.KU_SC, alpha=0.1,
+                      dt=1e-16, seed=seed, **T, B0=1.0, direction=B)
+    S = np.ascontiguousarray(S0.copy())
+    orc.Oracle(p, grain).run(S, 0, 2)
+    assert np.max(np.abs(got2 - S)) < TOL64
+
+    # an output that partly overlaps the input is refused on the host
+    big = torch.zeros((2 * n, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(hamr.HamrError, match="overlaps") as e:
+        hamr.sllg_heun_step_noalloc((nx, ny, nz), big[:n], big[n // 2:n // 2 + n], step=0, **kw)
+    assert e.value.code == hamr.ERR_ARG
+
 
 def test_noalloc_rejects_oversize(env):
     torch, hamr, I = env
