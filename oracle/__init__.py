@@ -57,7 +57,7 @@ class OrcMsParams(ctypes.Structure):
         ("drv", OrcParams),
         ("profile", ctypes.c_int32), ("prof_wz", ctypes.c_double), ("prof_dz", ctypes.c_double),
         ("prof_Bx0", ctypes.c_double), ("prof_wx", ctypes.c_double), ("prof_dx", ctypes.c_double),
-        ("demag", ctypes.c_int32),
+        ("demag", ctypes.c_int32), ("margin", ctypes.c_int32),
     ]
 
 
@@ -371,9 +371,12 @@ class MsParams:
                  T_C=None, Ms0=None, A0=None, K0=None, dt=1e-16, gamma=C_GAMMA, seed=1,
                  T_amb=0.0, T_peak=0.0, fwhm=0.0, x0=0.0, y0=0.0, vx=0.0, vy=0.0,
                  B0=0.0, direction=(0.0, 0.0, 1.0), bits=(), bit_len=1.0, ramp_len=0.0,
-                 head_x0=0.0, head_v=0.0, profile=None, demag=False):
+                 head_x0=0.0, head_v=0.0, profile=None, demag=False, margin=-1):
         self.ncx, self.ncy, self.ncz = int(ncx), int(ncy), int(ncz)
         self.demag = bool(demag)
+        # simulated region: the window and `margin` cell columns on each side are evolved, the
+        # rest of the track is frozen (margin < 0: the whole track is evolved)
+        self.margin = int(margin)
         # head profile: dict(wz=, dz=, Bx0=, wx=, dx=) or None for a uniform field
         self.profile = dict(profile) if profile else None
         self.cell, self.ratio, self.wx = float(cell), int(ratio), int(wx)
@@ -408,6 +411,7 @@ class MsParams:
         s.lambda_, s.T_C = self.lam, self.T_C
         s.drv = self.drv.struct()
         s.demag = int(self.demag)
+        s.margin = self.margin
         if self.profile:
             s.profile = 1
             s.prof_wz, s.prof_dz = self.profile["wz"], self.profile["dz"]

@@ -59,6 +59,9 @@ typedef struct {
     double prof_Bx0;        /* amplitude of the in-plane (x) component [T] */
     double prof_wx, prof_dx; /* its width and offset from the head [m] */
     int32_t demag;          /* 1: add the demagnetising field of Eq. 7 in both regions */
+    int32_t margin;         /* < 0: every micromagnetic cell is evolved; >= 0: only the cells of the
+                               simulated region, columns [ox - margin, ox + wx + margin), are; the
+                               others are frozen (Sec. II, Fig. 1) */
 } orc_ms_params;
 
 typedef struct {
@@ -75,6 +78,8 @@ typedef struct {
     int32_t live;           /* 1: the window's sites are newer than its cells (placed, and the
                                cells not replaced since) */
     double *Bd;             /* [3 nc] demagnetising field of the current step [T], or NULL */
+    double *me_store;       /* [nc] m_e of each cell at its last evolved step (or the window's
+                               placement): the m_e of a frozen cell */
 } orc_ms;
 
 /* ------------------------------------------------------------------------- */
@@ -184,7 +189,7 @@ int64_t orc_ms_window_sites(const orc_ms_params *p)
 void orc_ms_destroy(orc_ms *c)
 {
     if (!c) return;
-    free(c->bits); free(c->grain); free(c->m); free(c->S); free(c->Bd);
+    free(c->bits); free(c->grain); free(c->m); free(c->S); free(c->Bd); free(c->me_store);
     free(c);
 }
 
@@ -205,6 +210,11 @@ orc_ms *orc_ms_create(const orc_ms_params *p, const int32_t *cell_grain)
     c->nw = orc_ms_window_sites(p);
     c->S = (double *)calloc(3 * (size_t)c->nw, sizeof(double));
     c->Bd = (double *)calloc(3 * (size_t)c->nc, sizeof(double));
+    c->me_store = (double *)calloc((size_t)c->nc, sizeof(double));
+    if (!c->grain || !c->m || !c->S || !c->Bd || !c->me_store) {
+        orc_ms_destroy(c);
+        return NULL;
+    }
     return c;
 }
 
@@ -317,6 +327,25 @@ static void thermalise(orc_ms *c, int32_t cx0, int32_t cx1, double t, uint64_t e
             }
 }
 
+/* Whether cell column cx is in the simulated region (every column without a region). */
+static int in_region(const orc_ms *c, int64_t cx)
+{
+    const int32_t g = c->p.margin;
+    return g < 0 || (cx >= (int64_t)c->ox - g && cx < (int64_t)c->ox + c->p.wx + g);
+}
+
+/* m_e(T(t), |B_app(t)|) of every magnetic cell into me_store. */
+static void store_me(orc_ms *c, double t)
+{
+    const orc_ms_params *p = &c->p;
+    for (int64_t q = 0; q < c->nc; ++q) {
+        if (c->grain[q] < 0) continue;
+        double B[3];
+        orc_ms_field(p, (q % p->ncx + 0.5) * p->cell, t, B);
+        c->me_store[q] = orc_me(p->T_C, cell_temperature(c, q, t), p->mu_s, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+    }
+}
+
 /* Place the window at cell column ox and thermalise all of it from the cells.  A window that
  * is already placed first hands its sites back to its cells by Eq. 6, as the trailing column
  * does when the window moves (Sec. II), unless the cells have been replaced since. */
@@ -326,6 +355,8 @@ int orc_ms_set_window(orc_ms *c, int32_t ox)
     if (c->live) average_cells(c, c->ox, c->ox + c->p.wx);
     c->live = 1;
     c->ox = ox;
+    /* every cell's m_e at the placement: a cell that stays frozen keeps it */
+    store_me(c, (double)c->step * c->p.drv.dt);
     thermalise(c, ox, ox + c->p.wx, (double)c->step * c->p.drv.dt, (uint64_t)c->events);
     c->events += 1;
     return 0;
@@ -495,7 +526,11 @@ static int mm_step(orc_ms *c)
         T[q] = cell_temperature(c, q, t);
         me[q] = orc_me(p->T_C, T[q], p->mu_s, Bm);
     }
-#define ORC_EVOLVED(q) (c->grain[q] >= 0 && ((q) % p->ncx < c->ox || (q) % p->ncx >= c->ox + p->wx))
+    /* the simulated region's cells keep this step's m_e; frozen cells keep theirs */
+    for (int64_t q = 0; q < nc; ++q)
+        if (c->grain[q] >= 0 && in_region(c, q % p->ncx)) c->me_store[q] = me[q];
+#define ORC_EVOLVED(q) \
+    (c->grain[q] >= 0 && ((q) % p->ncx < c->ox || (q) % p->ncx >= c->ox + p->wx) && in_region(c, (q) % p->ncx))
     memcpy(V, c->m, sizeof(double) * 3 * (size_t)nc);
     const double cstage[4] = {0.5, 0.5, 1.0, 0.0}, wstage[4] = {1.0, 2.0, 2.0, 1.0};
     for (int s = 0; s < 4; ++s) {
@@ -549,9 +584,13 @@ static int demag_stage(orc_ms *c)
                         for (int d = 0; d < 3; ++d) M[3 * q + d] += p->mu_s / V * Si[d];
                     }
         } else {
-            double B[3];
-            orc_ms_field(p, (cx + 0.5) * p->cell, t, B);
-            double me = orc_me(p->T_C, cell_temperature(c, q, t), p->mu_s, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+            /* a frozen cell (outside the simulated region) keeps its stored m_e */
+            double me = c->me_store[q];
+            if (in_region(c, cx)) {
+                double B[3];
+                orc_ms_field(p, (cx + 0.5) * p->cell, t, B);
+                me = orc_me(p->T_C, cell_temperature(c, q, t), p->mu_s, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+            }
             for (int d = 0; d < 3; ++d) M[3 * q + d] = p->Ms0 * me * c->m[3 * q + d];
         }
     }

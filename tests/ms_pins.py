@@ -611,6 +611,91 @@ def check_window_replacement_hands_back():
     assert np.array_equal(O.cells(), m0)
 
 
+def check_region_frozen_end_spin_wave():
+    """Simulated region (Sec. II, Fig. 1): cells beyond it are frozen, so the region's edge
+    cell sees a neighbour that does not move.  A chain of N region cells with a free end (a
+    non-magnetic cell) and a frozen end (cells held along +z) carries small standing waves
+    m_x + i m_y = eps cos(th (j + 1/2)), th = (2n - 1) pi / (2N + 1), the modes of the
+    Laplacian with one missing and one fixed neighbour (eigenvalue 2 - 2 cos th), precessing
+    at gamma [B + 2 K0 m_e^2 / Ms0 + (2 A0 m_e / Ms0)(2 - 2 cos th) / c^2]."""
+    N, F, c, T, B0, eps = 12, 6, 1e-9, 400.0, 0.5, 1e-4
+    p = o.MsParams(N + F + 1, 1, 1, c, 4, 1, J=J_SC, ku=KU, lam=0.0, dt=1e-16, T_amb=T, B0=B0,
+                   direction=(0, 0, 1), A0=J_SC / (2 * A), Ms0=MU_S / A ** 3, K0=KU / A ** 3, margin=N)
+    grain = np.zeros(N + F + 1, np.int32)
+    grain[0] = -1                       # the window's cell: no atomistic sites
+    me = o.me(p.T_C, T, MU_S, B0)
+    for n in (1, 2):
+        th = (2 * n - 1) * math.pi / (2 * N + 1)
+        O = o.MsOracle(p, grain)
+        j = np.arange(N)
+        amp = eps * np.cos(th * (j + 0.5))
+        m = np.zeros((N + F + 1, 3))
+        m[:, 2] = 1.0
+        m[1:N + 1, 0] = amp
+        m[1:N + 1, 2] = np.sqrt(1 - amp ** 2)
+        O.set_cells(m)
+        O.set_window(0)
+        steps = 300
+        O.run(steps)
+        got = O.cells()
+        assert np.array_equal(got[N + 1:], m[N + 1:])      # the frozen cells did not move
+        w = G * (B0 + 2 * p.K0 * me ** 2 / p.Ms0 + 2 * p.A0 * me / p.Ms0 * (2 - 2 * math.cos(th)) / c ** 2)
+        ph = np.arctan2(got[1:N + 1, 1], got[1:N + 1, 0])
+        want = w * steps * p.drv.dt
+        assert abs((ph[0] - want + math.pi) % (2 * math.pi) - math.pi) < 1e-4 * want, (n, ph[0], want)
+
+
+def _region_pair(margin, demag, steps, seed=3):
+    """The same moving-window run with the whole track evolved and with a simulated region."""
+    kw = dict(J=J_SC, ku=KU, dt=1e-16, T_amb=300.0, T_peak=1300.0, fwhm=5e-9, x0=7.3e-9, y0=2e-9, vx=2.5e5,
+              B0=1.2, direction=(0.1, 0.0, -1.0), seed=seed, demag=demag)
+    grain = np.zeros(30 * 4 * 2, np.int32)
+    grain.reshape(2, 4, 30)[:, :, 17] = -1
+    out = []
+    for g in (-1, margin):
+        p = o.MsParams(30, 4, 2, 1e-9, 2, 6, margin=g, **kw)
+        O = o.MsOracle(p, grain)
+        O.set_cells(_tilted(p.n_cells, seed, 30.0) * (grain >= 0)[:, None])
+        O.set_window(o.ms_target(p, 0.0))
+        O.run(steps, follow=True)
+        out.append(O)
+    return out
+
+
+def check_region_covering_track_is_whole_track():
+    """A simulated region at least as long as the track evolves every cell: bitwise the
+    whole-track run, window moves and the demagnetising field included."""
+    a, b = _region_pair(40, True, 40)
+    assert a.window == b.window > o.ms_target(a.p, 0.0)
+    assert np.array_equal(a.cells(), b.cells()) and np.array_equal(a.moments(), b.moments())
+
+
+def check_region_first_step_and_frozen_cells():
+    """One coupled step with a simulated region: the window and the region's cells at least
+    four columns inside its edges are bitwise the whole-track step (an edge cell sees a frozen
+    neighbour's m in the four RK4 stages, the whole track a moving one, and that difference
+    moves one column per stage; the demagnetising field of the frozen cells uses the m_e stored
+    at the placement, the current one on the first step), and the frozen cells do not move;
+    over a longer run the cells ahead of the region stay as they were."""
+    a, b = _region_pair(6, True, 1)
+    ox, cols = b.window, np.arange(30)
+    region = (cols >= ox - 6) & (cols < ox + 6 + 6)
+    inner = (cols >= ox - 2) & (cols < ox + 6 + 2)
+    ca, cb = a.cells().reshape(2, 4, 30, 3), b.cells().reshape(2, 4, 30, 3)
+    assert np.array_equal(ca[:, :, inner], cb[:, :, inner])
+    assert np.array_equal(a.moments(), b.moments())
+    c0 = _tilted(30 * 4 * 2, 3, 30.0).reshape(2, 4, 30, 3)
+    mag = np.ones((2, 4, 30), bool)
+    mag[:, :, 17] = False
+    out = ~region
+    assert np.array_equal(cb[:, :, out][mag[:, :, out]], c0[:, :, out][mag[:, :, out]])
+    assert not np.array_equal(ca[:, :, out], cb[:, :, out])
+    a, b = _region_pair(3, False, 40)
+    ahead = cols >= b.window + 6 + 3
+    cb = b.cells().reshape(2, 4, 30, 3)
+    assert ahead.any() and np.array_equal(cb[:, :, ahead][mag[:, :, ahead]], c0[:, :, ahead][mag[:, :, ahead]])
+
+
 FAST_CHECKS = [
     check_langevin_branches, check_me_limits, check_micromagnetic_damping_law,
     check_theta_max_printed_values, check_cone_distribution, check_eq6_average_brute_force,
@@ -619,5 +704,6 @@ FAST_CHECKS = [
     check_shift_moves_spins, check_window_target, check_read_track, check_head_profile_shape,
     check_isolated_cell_and_site_in_head_profile, check_demag_tensor_limits, check_demag_uniform_film,
     check_demag_in_coupled_step, check_set_drivers_continues_run, check_second_pass_keeps_written_tracks,
-    check_window_replacement_hands_back,
+    check_window_replacement_hands_back, check_region_frozen_end_spin_wave,
+    check_region_covering_track_is_whole_track, check_region_first_step_and_frozen_cells,
 ]

@@ -65,6 +65,10 @@ MUTANTS = [
     ("new drivers ignored", "    c->p = *p;\n    c->p.drv.bits = bits;", "    c->p.drv.bits = bits;"),
     ("new drivers reset the step count", "    c->p = *p;\n    c->p.drv.bits = bits;",
      "    c->p = *p;\n    c->p.drv.bits = bits;\n    c->step = 0;"),
+    ("simulated region one column longer", "cx < (int64_t)c->ox + c->p.wx + g", "cx <= (int64_t)c->ox + c->p.wx + g"),
+    ("frozen cells evolved", "((q) % p->ncx < c->ox || (q) % p->ncx >= c->ox + p->wx) && in_region(c, (q) % p->ncx))",
+     "((q) % p->ncx < c->ox || (q) % p->ncx >= c->ox + p->wx))"),
+    ("frozen cells' m_e never stored", "    store_me(c, (double)c->step * c->p.drv.dt);\n", ""),
 ]
 
 
