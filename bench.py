@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-ms", action="store_true", help="skip the multiscale-track line")
     p.add_argument("--ms-steps", type=int, default=20)
+    p.add_argument("--ms-margin", type=int, default=-1,
+                   help="multiscale_track: evolve only the window and this many cell columns on each side")
+    p.add_argument("--ms-ncx", type=int, default=500, help="multiscale_track: track length in cells")
     p.add_argument("--ms-demag", action="store_true",
                    help="with --workload multiscale_track: the demagnetising field on")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -327,6 +330,38 @@ def cpu_baseline_one_core(workload, seconds):
         return None
 
 
+def ms_rate(w, precision, K, dist, demag=False, margin=-1):
+    """ms per coupled step of the multiscale track w from +z cells, the window following the
+    spot (CUDA events on the library's stream, max over ranks), after 3 untimed steps."""
+    import torch
+    from paper_2502_02236_gb300.hamr import Multiscale
+    G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                   ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
+                   seed=w["seed"] ^ (dist.rank << 48), precision=precision)
+    G.set_grain_map(w["grain"])
+    G.set_temperature_profile(**w["T"])
+    G.set_field_sequence(**w["field"])
+    m = np.zeros((w["ncx"] * w["ncy"] * w["ncz"], 3))
+    m[:, 2] = 1.0
+    G.set_cells(m)
+    G.set_region(margin)
+    G.set_window(int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5)))
+    if demag:
+        G.set_demag(True)
+    G.steps(3, follow=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.steps(K, follow=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    G.close()
+    return ms / K
+
+
 def multiscale_line(args, dist):
     """The full multiscale track (500 x 60 x 10 nm of 1 nm micromagnetic cells with a 60 nm
     atomistic window of 240 x 240 x 40 sites at 0.25 nm, window following the laser), FP32
@@ -381,6 +416,17 @@ def multiscale_line(args, dist):
             "fp32_with_demag": {"ms_per_step": t32d, "window_spin_steps_per_s": nw * dist.world / (t32d / 1e3),
                                 "steps": K, "note": "Eq. 7 by FFT convolution on the 1000 x 120 x 20 padded grid"},
             "launches_per_step": 10, "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot"}
+    # the simulated region (Sec. II, Fig. 1): the window and 60 cell columns on each side evolve,
+    # the rest of the track is frozen; the step's cost follows the region, not the track
+    reg = {}
+    for ncx in (500, 2000):
+        wt = I.multiscale_track(ncx=ncx)
+        reg[str(ncx)] = {"ms_per_step": ms_rate(wt, "fp32", 5 * K, dist, margin=60),
+                         "ms_per_step_demag": ms_rate(wt, "fp32", K, dist, demag=True, margin=60),
+                         "cells": ncx * wt["ncy"] * wt["ncz"]}
+    line["region"] = {"margin_cells": 60, "dtype": "f32", "tracks_by_ncx": reg,
+                      "note": "track lengths of 500 and 2000 cells; Eq. 7 with the region's own field on a "
+                              "360-column padded grid each step and the frozen track's field kept between moves"}
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
         import oracle as orc
         T, F = w["T"], w["field"]
@@ -417,7 +463,7 @@ def multiscale_only(args, dist):
     import torch
     from paper_2502_02236_gb300 import inputs as I
     from paper_2502_02236_gb300.hamr import Multiscale
-    w = I.multiscale_track()
+    w = I.multiscale_track(ncx=args.ms_ncx)
     G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"], ku=w["ku"],
                    Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
                    seed=w["seed"] ^ (dist.rank << 48), precision="fp32")
@@ -427,6 +473,7 @@ def multiscale_only(args, dist):
     m = np.zeros((G.n_cells, 3))
     m[:, 2] = 1.0
     G.set_cells(m)
+    G.set_region(args.ms_margin)
     G.set_window(int(np.floor(w["T"]["x0"] / w["cell"] - w["wx"] / 2 + 0.5)))
     if args.ms_demag:
         G.set_demag(True)
@@ -447,7 +494,7 @@ def multiscale_only(args, dist):
            "unit": "spin-steps/s", "n_gpus": dist.world, "steps": K, "warmup": max(3, args.warmup),
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": {"workload": "multiscale_track", "demag": bool(args.ms_demag),
-                                           "window_sites": nw, "cells": G.n_cells}}
+                                           "window_sites": nw, "cells": G.n_cells, "margin": args.ms_margin}}
     if dist.rank == 0:
         print(json.dumps(out), flush=True)
     dist.close()

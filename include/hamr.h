@@ -358,6 +358,13 @@ int hamr_ms_set_field_sequence(hamr_ms_t h, double B0, const double dir[3], cons
  * m_e(T) law.  wz <= 0 restores the spatially uniform field B0 s(t) dir.  ARG on non-finite
  * values or wx <= 0. */
 int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, double wx, double dx);
+/* Simulated region (Sec. II, Fig. 1): margin >= 0 evolves only the micromagnetic cells of
+ * the cell columns [x0 - margin, x0 + wx + margin) around the window (x0 its first column),
+ * a region that moves with the window; every other cell is frozen: it keeps its m and the
+ * m_e(T) of its last evolved step, or of the window's last placement (its magnetisation in
+ * Eq. 7).  The cost of a step then follows the region, not the track.  margin < 0 (the
+ * default) evolves the whole track.  Takes effect from the next step.  Errors: ARG (NULL). */
+int hamr_ms_set_region(hamr_ms_t h, int32_t margin);
 /* Demagnetising and stray field (Eq. 7) in both regions: B_d = -mu0 N * M on every cell,
  * with N the demagnetising tensor of cubic cells (Newell, Williams and Dunlop, J. Geophys.
  * Res. 98, 9551 (1993); the point-dipole tensor beyond 40 cell edges), M = Ms0 m_e(T) m on

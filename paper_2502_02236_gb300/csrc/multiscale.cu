@@ -387,9 +387,10 @@ __global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real
 // spot T is the ambient temperature to the last bit.
 template <typename Real>
 __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, const int *grain, MsDev P,
-                          ReplicaDev D, double t, Field<double> F, double Bm_last) {
+                          ReplicaDev D, double t, Field<double> F, double Bm_last, int cx0, int ncol) {
     int cx, cy, cz;
-    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    if (!coords(ncol, P.ncy, cx, cy, cz)) return;
+    cx += cx0;
     const int q0 = cell_at(P, cx, cy, 0), lz = P.ncx * P.ncy;
     const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
     const V3<double> B = field_at(P, F, (cx + 0.5) * P.cell);
@@ -423,17 +424,21 @@ __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, c
     }
 }
 
-// One RK4 stage on the evolved cells: K = dm/dt at the stage values Vin, acc += w K and
-// Vout = m + c dt K (the next stage's values).  A window cell writes its Eq. 6 direction m
-// to Vout, so that every stage buffer holds m there (stage 0 reads m itself); non-magnetic
-// cells are never read.  The cell's grain code, its stage value and its neighbours' grain
+// One RK4 stage on the evolved cells, the magnetic cells of columns [c0, c1) outside the
+// window: K = dm/dt at the stage values Vin, acc += w K and Vout = m + c dt K (the next
+// stage's values).  A window cell, and a frozen cell next to the simulated region, writes its
+// m to Vout, so that every stage buffer holds m there (stage 0 reads m itself); the launch
+// covers [e0, e1), one column beyond the region on each side.  Non-magnetic cells are never
+// read.  The cell's grain code, its stage value and its neighbours' grain
 // codes are loaded together before the tests: the threads are short and bound by memory
 // latency.
 template <typename Real>
 __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first) {
+                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first, int e0, int ne,
+                           int c0, int c1) {
     int cx, cy, cz;
-    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    if (!coords(ne, P.ncy, cx, cy, cz)) return;
+    cx += e0;
     const int q = cell_at(P, cx, cy, cz), lz = P.ncx * P.ncy;
     const int g = grain[q];
     const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
@@ -446,7 +451,7 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     for (int b = 0; b < 6; ++b) gn[b] = grain[qn[b]];
     if (g < 0) return;
     const Real mx = m[q], my = m[P.nc + q], mz = m[2 * P.nc + q];
-    if (cx >= ox && cx < ox + P.wx) {   // a window cell: not evolved here
+    if ((cx >= ox && cx < ox + P.wx) || cx < c0 || cx >= c1) {  // a window or frozen cell: not evolved here
         Vout[q] = mx;
         Vout[P.nc + q] = my;
         Vout[2 * P.nc + q] = mz;
@@ -485,9 +490,10 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
 }
 
 template <typename Real>
-__global__ void k_mm_final(Real *m, const Real *acc, const int *grain, MsDev P, int ox) {
+__global__ void k_mm_final(Real *m, const Real *acc, const int *grain, MsDev P, int ox, int c0, int ncol) {
     int cx, cy, cz;
-    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+    if (!coords(ncol, P.ncy, cx, cy, cz)) return;
+    cx += c0;
     const int q = cell_at(P, cx, cy, cz);
     if (grain[q] < 0 || (cx >= ox && cx < ox + P.wx)) return;
     const Real h6 = (Real)P.dt / Real(6);
@@ -621,18 +627,22 @@ struct Pad {
     long long Ptot, Pc;   // real points, complex points (Px / 2 + 1 along x)
 };
 
-// The cells' magnetisation in the padded layout: window cells M = (mu_s / V) sum of their
-// spins (Eq. 6; wn holds the sum's length and m its direction, from the window average of
-// the same state), other magnetic cells M = Ms0 m_e m, non-magnetic cells 0.
+// The cells' magnetisation in the padded layout of a grid whose first column is g0 (ncol
+// columns): window cells M = (mu_s / V) sum of their spins (Eq. 6; wn holds the sum's length
+// and m its direction, from the window average of the same state), other magnetic cells
+// M = Ms0 m_e m (a frozen cell's m_e is the stored one), non-magnetic cells and columns beyond
+// the track 0.  mode selects the sources: 0 every cell, 1 the columns [s0, s1) only, 2 all
+// but those.
 template <typename Real>
 __global__ void k_demag_M(Real *Mpad, const Real *wn, const Real *m, const double *me, const int *grain, MsDev P,
-                          Pad pd, int ox) {
-    int cx, cy, cz;
-    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
-    const int q = cell_at(P, cx, cy, cz);
-    const long long pp = cx + (long long)pd.Px * (cy + (long long)pd.Py * cz);
+                          Pad pd, int ox, int g0, int ncol, int s0, int s1, int mode) {
+    int i, cy, cz;
+    if (!coords(ncol, P.ncy, i, cy, cz)) return;
+    const int cx = g0 + i;
+    const long long pp = i + (long long)pd.Px * (cy + (long long)pd.Py * cz);
     Real Mx = 0, My = 0, Mz = 0;
-    if (grain[q] >= 0) {
+    const int q = cx < P.ncx ? cell_at(P, cx, cy, cz) : 0;
+    if (cx < P.ncx && grain[q] >= 0 && (mode == 0 || (mode == 1) == (cx >= s0 && cx < s1))) {
         // a window cell: (mu_s / V) |sum of its sites| times their direction, both from Eq. 6
         // of this step; a cell outside: Ms0 m_e(T) m
         const Real a = (cx >= ox && cx < ox + P.wx) ? (Real)(P.mu_s / (P.cell * P.cell * P.cell)) * wn[q]
@@ -671,18 +681,55 @@ __global__ void k_demag_multiply(C *Mh, const C *Nh, long long Pc) {
     Mh[2 * Pc + f] = add3(mul(nxz, mx), mul(nyz, my), mul(nzz, mz));
 }
 
-// B_d = -mu0 H on every cell (the inverse transform is unnormalised: divide by Ptot)
+// B_d = -mu0 H on the cells of the target columns [t0, t1) of a grid whose first column is g0
+// (the inverse transform is unnormalised: divide by Ptot), plus `add` where given.
 template <typename Real>
-__global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd) {
-    int cx, cy, cz;
-    if (!coords(P.ncx, P.ncy, cx, cy, cz)) return;
+__global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd, int g0, int ncol, int t0, int t1,
+                                const Real *add) {
+    int i, cy, cz;
+    if (!coords(ncol, P.ncy, i, cy, cz)) return;
+    const int cx = g0 + i;
+    if (cx < t0 || cx >= t1 || cx >= P.ncx) return;
     const int q = cell_at(P, cx, cy, cz);
-    const long long pp = cx + (long long)pd.Px * (cy + (long long)pd.Py * cz);
+    const long long pp = i + (long long)pd.Px * (cy + (long long)pd.Py * cz);
     const Real s = (Real)(-1.25663706212e-6 / (double)pd.Ptot);
-    Bd[q] = s * Hpad[pp];
-    Bd[P.nc + q] = s * Hpad[pd.Ptot + pp];
-    Bd[2 * P.nc + q] = s * Hpad[2 * pd.Ptot + pp];
+    Real bx = s * Hpad[pp], by = s * Hpad[pd.Ptot + pp], bz = s * Hpad[2 * pd.Ptot + pp];
+    if (add) {
+        bx += add[q];
+        by += add[P.nc + q];
+        bz += add[2 * P.nc + q];
+    }
+    Bd[q] = bx;
+    Bd[P.nc + q] = by;
+    Bd[2 * P.nc + q] = bz;
 }
+
+// One zero-padded convolution grid of Eq. 7 over ncol cell columns (all of y and z): the
+// tensor's spectra [6][Pc], the padded M | H buffer [6][Ptot], the transformed M [3][Pc] and
+// the cuFFT plans (three transforms per call).
+struct DemagGrid {
+    int ncol = 0;
+    Pad pd{};
+    void *Nh = nullptr, *Mpad = nullptr, *Mh = nullptr;
+    cufftHandle plan_f = 0, plan_b = 0;
+    bool plans = false;
+};
+
+void demag_grid_free(DemagGrid &g) {
+    void **b[] = {&g.Nh, &g.Mpad, &g.Mh};
+    for (void **p : b)
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    if (g.plans) {
+        cufftDestroy(g.plan_f);
+        cufftDestroy(g.plan_b);
+        g.plans = false;
+    }
+    g.ncol = 0;
+}
+
 
 constexpr int BLK = 256;
 inline unsigned nblk(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
@@ -713,16 +760,19 @@ struct hamr_ms_ctx {
     double Bm_last = NAN;         // field magnitude of the last m_e solve
     double *stage = nullptr;      // AoS FP64 staging for host copies
     int ox = -1;                  // window column (-1: not placed)
+    int margin = -1;              // simulated region: the window and `margin` columns on each side (< 0: the track)
     long long step = 0;
     long long events = 0;         // thermalisation events so far
     bool grains_set = false, cells_set = false;
     bool window_live = false;     // the window's sites are newer than its cells (placed, cells not replaced since)
-    // demagnetising field (Eq. 7): padded grid, tensor spectra [6][Pc], work arrays, plans
+    // demagnetising field (Eq. 7): the track's padded grid and, with a simulated region, the
+    // region's; B_d [3][nc]; the frozen cells' part of B_d on the region's cells [3][nc], valid
+    // for the region [fz_c0, fz_c1) until the frozen cells change
     bool demag = false;
-    Pad pad{};
-    void *Nh = nullptr, *Mpad = nullptr, *Mh = nullptr, *Bd = nullptr;
-    cufftHandle plan_f = 0, plan_b = 0;
-    bool plans = false;
+    DemagGrid gtrack, gregion;
+    void *Bd = nullptr, *Bfz = nullptr;
+    int fz_c0 = -1, fz_c1 = -1;
+    bool fz_dirty = true;
 };
 
 namespace {
@@ -769,17 +819,14 @@ void ms_free(hamr_ms_t h) {
             cudaFree(*b);
             *b = nullptr;
         }
-    void **dbufs[] = {&h->Nh, &h->Mpad, &h->Mh, &h->Bd};
+    void **dbufs[] = {&h->Bd, &h->Bfz};
     for (void **b : dbufs)
         if (*b) {
             cudaFree(*b);
             *b = nullptr;
         }
-    if (h->plans) {
-        cufftDestroy(h->plan_f);
-        cufftDestroy(h->plan_b);
-        h->plans = false;
-    }
+    demag_grid_free(h->gtrack);
+    demag_grid_free(h->gregion);
     if (h->wn) cudaFree(h->wn);
     if (h->me) cudaFree(h->me);
     if (h->me_prev) cudaFree(h->me_prev);
@@ -926,17 +973,19 @@ int pad_offset(int i, int n, int P) {
     return INT32_MIN;
 }
 
+// The tensor of Eq. 7 on the padded grid of ncol columns (host, FP64, in parallel over z
+// planes), its transform and the plans.
 template <typename Real>
-int ms_demag_setup(hamr_ms_t h) {
+int demag_grid_setup(hamr_ms_t h, DemagGrid &g, int ncol) {
     typedef typename std::conditional<sizeof(Real) == 8, cufftDoubleComplex, cufftComplex>::type C;
     const MsDev &P = h->P;
-    Pad &pd = h->pad;
-    pd.Px = P.ncx > 1 ? 2 * P.ncx : 1;
+    Pad &pd = g.pd;
+    g.ncol = ncol;
+    pd.Px = ncol > 1 ? 2 * ncol : 1;
     pd.Py = P.ncy > 1 ? 2 * P.ncy : 1;
     pd.Pz = P.ncz > 1 ? 2 * P.ncz : 1;
     pd.Ptot = (long long)pd.Px * pd.Py * pd.Pz;
     pd.Pc = (long long)(pd.Px / 2 + 1) * pd.Py * pd.Pz;
-    // tensor on the padded grid, on the host, in parallel over z planes
     std::vector<double> T(6 * (size_t)pd.Ptot, 0.0);
     const unsigned nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
@@ -949,7 +998,7 @@ int ms_demag_setup(hamr_ms_t h) {
                     const int Y = pad_offset(j, P.ncy, pd.Py);
                     if (Y == INT32_MIN) continue;
                     for (int i = 0; i < pd.Px; ++i) {
-                        const int X = pad_offset(i, P.ncx, pd.Px);
+                        const int X = pad_offset(i, ncol, pd.Px);
                         if (X == INT32_MIN) continue;
                         double N[6];
                         demag_tensor(X * P.cell, Y * P.cell, Z * P.cell, P.cell, N);
@@ -961,68 +1010,112 @@ int ms_demag_setup(hamr_ms_t h) {
         });
     for (auto &t : pool) t.join();
     std::vector<Real> Tr(T.begin(), T.end());
-    MSCK(h, cudaMalloc(&h->Nh, sizeof(C) * 6 * pd.Pc));
-    MSCK(h, cudaMalloc(&h->Mh, sizeof(C) * 3 * pd.Pc));
+    MSCK(h, cudaMalloc(&g.Nh, sizeof(C) * 6 * pd.Pc));
+    MSCK(h, cudaMalloc(&g.Mh, sizeof(C) * 3 * pd.Pc));
     // [M | H], each 3 padded grids; the tensor's six components pass through it once at setup
-    MSCK(h, cudaMalloc(&h->Mpad, sizeof(Real) * 6 * pd.Ptot));
-    MSCK(h, cudaMalloc(&h->Bd, sizeof(Real) * 3 * P.nc));
+    MSCK(h, cudaMalloc(&g.Mpad, sizeof(Real) * 6 * pd.Ptot));
     int n[3] = {pd.Pz, pd.Py, pd.Px};
     const bool dbl = sizeof(Real) == 8;
-    if (cufftPlanMany(&h->plan_f, 3, n, nullptr, 1, (int)pd.Ptot, nullptr, 1, (int)pd.Pc, dbl ? CUFFT_D2Z : CUFFT_R2C,
+    if (cufftPlanMany(&g.plan_f, 3, n, nullptr, 1, (int)pd.Ptot, nullptr, 1, (int)pd.Pc, dbl ? CUFFT_D2Z : CUFFT_R2C,
                       3) != CUFFT_SUCCESS ||
-        cufftPlanMany(&h->plan_b, 3, n, nullptr, 1, (int)pd.Pc, nullptr, 1, (int)pd.Ptot, dbl ? CUFFT_Z2D : CUFFT_C2R,
+        cufftPlanMany(&g.plan_b, 3, n, nullptr, 1, (int)pd.Pc, nullptr, 1, (int)pd.Ptot, dbl ? CUFFT_Z2D : CUFFT_C2R,
                       3) != CUFFT_SUCCESS)
         return msfail(h, HAMR_ERR_CUDA, "cuFFT plan creation failed for a %d x %d x %d grid", pd.Px, pd.Py, pd.Pz);
-    h->plans = true;
-    cufftSetStream(h->plan_f, h->stream);
-    cufftSetStream(h->plan_b, h->stream);
-    MSCK(h, cudaMemcpyAsync(h->Mpad, Tr.data(), sizeof(Real) * 6 * pd.Ptot, cudaMemcpyHostToDevice, h->stream));
+    g.plans = true;
+    cufftSetStream(g.plan_f, h->stream);
+    cufftSetStream(g.plan_b, h->stream);
+    MSCK(h, cudaMemcpyAsync(g.Mpad, Tr.data(), sizeof(Real) * 6 * pd.Ptot, cudaMemcpyHostToDevice, h->stream));
     for (int half = 0; half < 2; ++half) {
-        Real *src = (Real *)h->Mpad + (size_t)half * 3 * pd.Ptot;
-        C *dst = (C *)h->Nh + (size_t)half * 3 * pd.Pc;
-        const cufftResult r = dbl ? cufftExecD2Z(h->plan_f, (cufftDoubleReal *)src, (cufftDoubleComplex *)dst)
-                                  : cufftExecR2C(h->plan_f, (cufftReal *)src, (cufftComplex *)dst);
+        Real *src = (Real *)g.Mpad + (size_t)half * 3 * pd.Ptot;
+        C *dst = (C *)g.Nh + (size_t)half * 3 * pd.Pc;
+        const cufftResult r = dbl ? cufftExecD2Z(g.plan_f, (cufftDoubleReal *)src, (cufftDoubleComplex *)dst)
+                                  : cufftExecR2C(g.plan_f, (cufftReal *)src, (cufftComplex *)dst);
         if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform of the tensor failed");
     }
-    MSCK(h, cudaMemsetAsync(h->Mpad, 0, sizeof(Real) * 6 * pd.Ptot, h->stream));
+    MSCK(h, cudaMemsetAsync(g.Mpad, 0, sizeof(Real) * 6 * pd.Ptot, h->stream));
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
 }
 
-// B_d = -mu0 N * M of the current state (the m_e of each cell must be current)
+// The demagnetising field on the target columns [t0, t1) from the sources that `mode` selects
+// (k_demag_M), through grid g placed at column g0, into out (plus `add` where given).
 template <typename Real>
-int ms_demag_step(hamr_ms_t h) {
+int demag_pass(hamr_ms_t h, DemagGrid &g, int g0, int mode, int s0, int s1, Real *out, int t0, int t1,
+               const Real *add) {
     typedef typename std::conditional<sizeof(Real) == 8, cufftDoubleComplex, cufftComplex>::type C;
     const MsDev &P = h->P;
-    const Pad &pd = h->pad;
-    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
-    k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Mpad, (const Real *)h->wn, (const Real *)h->m, h->me,
-                                                h->grain_d, P, pd, h->ox);
+    const Pad &pd = g.pd;
+    const dim3 gc = grid3(g.ncol, P.ncy, P.ncz);
+    k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)g.Mpad, (const Real *)h->wn, (const Real *)h->m, h->me,
+                                                h->grain_d, P, pd, h->ox, g0, g.ncol, s0, s1, mode);
     MSCK(h, cudaGetLastError());
     const bool dbl = sizeof(Real) == 8;
-    cufftResult r = dbl ? cufftExecD2Z(h->plan_f, (cufftDoubleReal *)h->Mpad, (cufftDoubleComplex *)h->Mh)
-                        : cufftExecR2C(h->plan_f, (cufftReal *)h->Mpad, (cufftComplex *)h->Mh);
+    cufftResult r = dbl ? cufftExecD2Z(g.plan_f, (cufftDoubleReal *)g.Mpad, (cufftDoubleComplex *)g.Mh)
+                        : cufftExecR2C(g.plan_f, (cufftReal *)g.Mpad, (cufftComplex *)g.Mh);
     if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform failed");
-    k_demag_multiply<C><<<nblk(pd.Pc), BLK, 0, h->stream>>>((C *)h->Mh, (const C *)h->Nh, pd.Pc);
+    k_demag_multiply<C><<<nblk(pd.Pc), BLK, 0, h->stream>>>((C *)g.Mh, (const C *)g.Nh, pd.Pc);
     MSCK(h, cudaGetLastError());
     // H goes to the second half of the buffer: the padding of M (first half) must stay zero
-    Real *H = (Real *)h->Mpad + 3 * pd.Ptot;
-    r = dbl ? cufftExecZ2D(h->plan_b, (cufftDoubleComplex *)h->Mh, (cufftDoubleReal *)H)
-            : cufftExecC2R(h->plan_b, (cufftComplex *)h->Mh, (cufftReal *)H);
+    Real *H = (Real *)g.Mpad + 3 * pd.Ptot;
+    r = dbl ? cufftExecZ2D(g.plan_b, (cufftDoubleComplex *)g.Mh, (cufftDoubleReal *)H)
+            : cufftExecC2R(g.plan_b, (cufftComplex *)g.Mh, (cufftReal *)H);
     if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT inverse transform failed");
-    k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>((Real *)h->Bd, H, P, pd);
+    k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>(out, H, P, pd, g0, g.ncol, t0, t1, add);
     MSCK(h, cudaGetLastError());
     return HAMR_OK;
 }
 
+// The simulated region's cell columns [c0, c1): the window and `margin` columns on each side,
+// within the track (the whole track when margin < 0).
+void ms_region(const hamr_ms_t h, int &c0, int &c1) {
+    if (h->margin < 0) {
+        c0 = 0;
+        c1 = h->P.ncx;
+        return;
+    }
+    c0 = std::max(0, h->ox - h->margin);
+    c1 = std::min(h->P.ncx, h->ox + h->P.wx + h->margin);
+}
+
+// B_d = -mu0 N * M of the current state (the m_e of each cell must be current).  With a
+// simulated region only its cells need B_d: their own part is a convolution over the region's
+// padded grid, every step; the frozen cells' part is a convolution over the track's grid with
+// the region left out, kept until the region moves or the frozen cells change.
 template <typename Real>
-int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t) {
+int ms_demag_step(hamr_ms_t h) {
+    const MsDev &P = h->P;
+    int c0, c1;
+    ms_region(h, c0, c1);
+    const int L = h->margin < 0 ? P.ncx : std::min(P.ncx, P.wx + 2 * h->margin);
+    if (L >= P.ncx) return demag_pass<Real>(h, h->gtrack, 0, 0, 0, P.ncx, (Real *)h->Bd, 0, P.ncx, nullptr);
+    if (h->gregion.ncol != L) {
+        demag_grid_free(h->gregion);
+        int rc = demag_grid_setup<Real>(h, h->gregion, L);
+        if (rc) return rc;
+    }
+    if (h->fz_dirty || c0 != h->fz_c0 || c1 != h->fz_c1) {
+        int rc = demag_pass<Real>(h, h->gtrack, 0, 2, c0, c1, (Real *)h->Bfz, c0, c1, nullptr);
+        if (rc) return rc;
+        h->fz_c0 = c0;
+        h->fz_c1 = c1;
+        h->fz_dirty = false;
+    }
+    return demag_pass<Real>(h, h->gregion, c0, 1, c0, c1, (Real *)h->Bd, c0, c1, (const Real *)h->Bfz);
+}
+
+// Thermalise the window sites of cell columns [cx0, cx1) at time t.  m_e(T) is solved first
+// on every cell (all = true: a placement, which also gives every frozen cell its m_e) or on
+// the simulated region (a move; the cells that just froze keep theirs).
+template <typename Real>
+int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t, bool all) {
     const long long n = (long long)(cx1 - cx0) * h->P.r * h->P.nyw * h->P.nzw;
     if (n <= 0) return HAMR_OK;
-    // m_e(T) of every cell at t, then the cone of each thermalised site from its cell's m_e
+    int c0 = 0, c1 = h->P.ncx;
+    if (!all) ms_region(h, c0, c1);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<grid3(h->P.ncx, h->P.ncy, 1), BLK3, 0, h->stream>>>(
-        h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last);
+    k_mm_prep<Real><<<grid3(c1 - c0, h->P.ncy, 1), BLK3, 0, h->stream>>>(
+        h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last, c0,
+        c1 - c0);
     h->Bm_last = Bm;
     k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
                                                           h->ox, cx0, cx1, (unsigned long long)h->events);
@@ -1072,11 +1165,14 @@ int ms_step(hamr_ms_t h) {
     Real *S = (Real *)h->S, *Sp = (Real *)h->Sp, *F1 = (Real *)h->F1, *BTH = (Real *)h->BTH, *m = (Real *)h->m;
     const double t = (double)h->step * P.dt;
     const Field<Real> F = field_of<Real>(h, t);
-    // m_e(T) of every cell at t_n, then (optionally) the demagnetising field of the state at t_n
-    const dim3 gc = grid3(P.ncx, P.ncy, P.ncz);
+    // m_e(T) at t_n of every cell of the simulated region (frozen cells keep theirs), then
+    // (optionally) the demagnetising field of the state at t_n
+    int c0, c1;
+    ms_region(h, c0, c1);
+    const int e0 = std::max(0, c0 - 1), e1 = std::min(P.ncx, c1 + 1);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<grid3(P.ncx, P.ncy, 1), BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P,
-                                                            h->D, t, field_of<double>(h, t), h->Bm_last);
+    k_mm_prep<Real><<<grid3(c1 - c0, P.ncy, 1), BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P,
+                                                              h->D, t, field_of<double>(h, t), h->Bm_last, c0, c1 - c0);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
     const Real *Bd = nullptr;
@@ -1102,10 +1198,13 @@ int ms_step(hamr_ms_t h) {
     for (int s = 0; s < 4; ++s) {
         const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
         Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
-        k_mm_stage<Real><<<gc, BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m, (const Real *)h->coef, h->grain_d, P, h->ox,
-                                              F, Bd, cst[s], wst[s], s == 0);
+        k_mm_stage<Real><<<grid3(e1 - e0, P.ncy, P.ncz), BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m,
+                                                                        (const Real *)h->coef, h->grain_d, P, h->ox,
+                                                                        F, Bd, cst[s], wst[s], s == 0, e0, e1 - e0,
+                                                                        c0, c1);
     }
-    k_mm_final<Real><<<gc, BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox);
+    k_mm_final<Real><<<grid3(c1 - c0, P.ncy, P.ncz), BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox, c0,
+                                                                   c1 - c0);
     MSCK(h, cudaGetLastError());
     h->step += 1;
     return HAMR_OK;
@@ -1119,7 +1218,7 @@ int ms_shift_forward(hamr_ms_t h, double t) {
     MSCK(h, cudaGetLastError());
     std::swap(h->S, h->S2);
     h->ox += 1;
-    return ms_thermalise<Real>(h, h->ox + h->P.wx - 1, h->ox + h->P.wx, t);
+    return ms_thermalise<Real>(h, h->ox + h->P.wx - 1, h->ox + h->P.wx, t, false);
 }
 
 // host FP64 AoS (already in h->stage) -> state planes, and back
@@ -1256,6 +1355,7 @@ int hamr_ms_set_grain_map(hamr_ms_t h, const int32_t *cell_grain) {
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     h->grains_set = true;
+    h->fz_dirty = true;
     return HAMR_OK;
 }
 
@@ -1323,6 +1423,13 @@ int hamr_ms_set_head_profile(hamr_ms_t h, double Bx0, double wz, double dz, doub
     return HAMR_OK;
 }
 
+int hamr_ms_set_region(hamr_ms_t h, int32_t margin) {
+    if (!h) return HAMR_ERR_ARG;
+    h->margin = margin < 0 ? -1 : margin;
+    h->fz_dirty = true;
+    return HAMR_OK;
+}
+
 int hamr_ms_set_demag(hamr_ms_t h, int32_t on) {
     if (!h) return HAMR_ERR_ARG;
     if (!on) {
@@ -1330,11 +1437,17 @@ int hamr_ms_set_demag(hamr_ms_t h, int32_t on) {
         return HAMR_OK;
     }
     MsDeviceGuard dg(h->device);
-    if (!h->plans) {
-        const int rc = h->prec == HAMR_FP64 ? ms_demag_setup<double>(h) : ms_demag_setup<float>(h);
+    if (!h->gtrack.plans) {
+        const size_t es = h->prec == HAMR_FP64 ? 8 : 4;
+        MSCK(h, cudaMalloc(&h->Bd, es * 3 * h->P.nc));
+        MSCK(h, cudaMalloc(&h->Bfz, es * 3 * h->P.nc));
+        MSCK(h, cudaMemsetAsync(h->Bd, 0, es * 3 * h->P.nc, h->stream));
+        const int rc = h->prec == HAMR_FP64 ? demag_grid_setup<double>(h, h->gtrack, h->P.ncx)
+                                            : demag_grid_setup<float>(h, h->gtrack, h->P.ncx);
         if (rc) return rc;
     }
     h->demag = true;
+    h->fz_dirty = true;
     return HAMR_OK;
 }
 
@@ -1350,6 +1463,7 @@ int hamr_ms_set_cells(hamr_ms_t h, const double *m) {
     MSCK(h, cudaStreamSynchronize(h->stream));
     h->cells_set = true;
     h->window_live = false;
+    h->fz_dirty = true;
     return HAMR_OK;
 }
 
@@ -1367,10 +1481,11 @@ int hamr_ms_set_window(hamr_ms_t h, int32_t x0_cells) {
         if (rc) return rc;
     }
     h->window_live = true;
+    h->fz_dirty = true;  // every cell's m_e is solved again at the placement
     h->ox = x0_cells;
     const double t = (double)h->step * h->P.dt;
-    int rc = h->prec == HAMR_FP64 ? ms_thermalise<double>(h, h->ox, h->ox + h->P.wx, t)
-                                  : ms_thermalise<float>(h, h->ox, h->ox + h->P.wx, t);
+    int rc = h->prec == HAMR_FP64 ? ms_thermalise<double>(h, h->ox, h->ox + h->P.wx, t, true)
+                                  : ms_thermalise<float>(h, h->ox, h->ox + h->P.wx, t, true);
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;

@@ -30,7 +30,7 @@ EXPORTS = [
     "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
     "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
     "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window", "hamr_ms_read_track",
-    "hamr_ms_set_head_profile", "hamr_ms_set_demag",
+    "hamr_ms_set_head_profile", "hamr_ms_set_demag", "hamr_ms_set_region",
     "hamr_ms_last_error", "hamr_ms_destroy",
 ]
 NOALLOC_MAX_SITES = 131072
@@ -135,6 +135,7 @@ def lib():
             "hamr_ms_read_track": [vp, d, d, i32, i32, i32, vp, vp],
             "hamr_ms_set_head_profile": [vp, d, d, d, d, d],
             "hamr_ms_set_demag": [vp, i32],
+            "hamr_ms_set_region": [vp, i32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -458,6 +459,11 @@ class Multiscale:
         """tanh profiles of the write field along the track following the head (wz <= 0: a
         spatially uniform field)."""
         self._ck(lib().hamr_ms_set_head_profile(self._h, Bx0, wz, dz, wx, dx))
+
+    def set_region(self, margin):
+        """Evolve only the window and `margin` cell columns on each side; the rest of the track
+        is frozen (margin < 0: the whole track)."""
+        self._ck(lib().hamr_ms_set_region(self._h, int(margin)))
 
     def set_demag(self, on=True):
         """The demagnetising field of Eq. 7 in both regions (FFT convolution)."""

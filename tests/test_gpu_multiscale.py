@@ -14,14 +14,14 @@ TOL = {"fp64": 1e-9, "fp32": 2e-4}
 PRECISIONS = ["fp64", "fp32"]
 
 
-def pair(w, precision="fp64", profile=None, demag=False):
+def pair(w, precision="fp64", profile=None, demag=False, margin=-1):
     """The oracle and the GPU handle for one multiscale input description."""
     T, F = w["T"], w["field"]
     p = orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                      ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
                      seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
                      bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"],
-                     profile=profile, demag=demag)
+                     profile=profile, demag=demag, margin=margin)
     O = orc.MsOracle(p, w["grain"])
     G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
                    ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
@@ -33,6 +33,8 @@ def pair(w, precision="fp64", profile=None, demag=False):
         G.set_head_profile(**profile)
     if demag:
         G.set_demag(True)
+    if margin >= 0:
+        G.set_region(margin)
     return p, O, G
 
 
@@ -334,3 +336,30 @@ def test_parallel_track_second_pass_matches_oracle(prec):
             sig, bits = G.read_track(0.0, 4e-9, 9, *band)
             osig, obits = O.read_track(0.0, 4e-9, 9, *band)
             assert np.abs(sig - osig).max() < TOL[prec]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("demag", [False, True])
+def test_simulated_region_matches_oracle(prec, demag):
+    """The simulated region (Sec. II, Fig. 1): only the window and three cell columns on each
+    side evolve, the rest of the track is frozen (m and the m_e of its last evolved step, which
+    enter Eq. 7); the region moves with the window through several moves."""
+    w = I.multiscale_track(ncx=36, ncy=5, ncz=2, cell=1e-9, ratio=2, wx=6, grain_d=5e-9, seed=31, v=2.5e5,
+                           x_spot=8.013e-9)
+    p, O, G = pair(w, prec, demag=demag, margin=3)
+    with G:
+        start(w, p, O, G, orc.ms_target(p, 0.0))
+        ox = O.window
+        m0 = O.cells().copy()
+        for block in (90, 110):
+            O.run(block, follow=True)
+            G.steps(block, follow=True)
+            dm, dS = compare(O, G)
+            assert dm < TOL[prec] and dS < TOL[prec], (block, dm, dS)
+            assert G.window()[0] == O.window
+        assert O.window >= ox + 4
+        ahead = np.arange(36) >= O.window + 6 + 3
+        cells = G.read_cells().reshape(2, 5, 36, 3)[:, :, ahead]
+        want = m0.reshape(2, 5, 36, 3)[:, :, ahead]
+        assert np.abs(cells - want).max() < (1e-15 if prec == "fp64" else 1e-7)   # frozen cells stay put
