@@ -4,8 +4,9 @@
 //
 // Per coupled step n -> n+1 (drivers frozen at t_n):
 //   1. k_ms_average   - Eq. 6: every window cell takes the direction of the sum of its sites;
-//   2. k_ms_predict,  - the sLLG Heun step of the window (Eq. 1-3); across the window's x
-//      k_ms_correct     faces a bond sees the direction of the micromagnetic cell there;
+//   2. k_ms_fused     - the sLLG Heun step of the window (Eq. 1-3), both stages in one pass;
+//                       across the window's x faces a bond sees the direction of the
+//                       micromagnetic cell there;
 //   3. k_mm_prep,     - one classical RK4 step of the micromagnetic LLG (Eq. 1 without the
 //      k_mm_stage x4,   thermal field; Eq. 4 on a 6-point Laplacian, Eq. 5) on the cells
 //      k_mm_final       outside the window, with Ms = Ms0 m_e, A = A0 m_e^2, K = K0 m_e^3,
@@ -241,137 +242,201 @@ __global__ void k_ms_average_w(Real *m, Real *wn, const Real *S, const int *grai
     }
 }
 
-// Sum of the neighbour directions v_j of window site (i, j, k) of grain g (cell qs) over its
-// same-grain bonds: the window spins V inside, the cells m across the window's x faces.  A
-// neighbour in the site's own cell is of grain g; only a neighbour across a cell face looks
-// up its grain, at cell qs +- 1, +- ncx or +- ncx ncy.  The caller scales the sum by J / mu_s.
-template <typename Real, int RT>
-__device__ __forceinline__ V3<Real> exchange(const MsDev &P, const Real *V, const Real *m, const int *grain, int ox,
-                                             int i, int j, int k, int g, int qs, long long s) {
-    const int r = RT ? RT : P.r;
-    const long long sy = P.nxw, sz = (long long)P.nxw * P.nyw;
-    const int cy = P.ncx, cz = P.ncx * P.ncy;
-    Real ex = 0, ey = 0, ez = 0;
-    auto site = [&](long long t) {
-        ex += V[t];
-        ey += V[P.nw + t];
-        ez += V[2 * P.nw + t];
-    };
-    auto cell = [&](int q) {
-        if (grain[q] != g) return;
-        ex += m[q];
-        ey += m[P.nc + q];
-        ez += m[2 * P.nc + q];
-    };
-    // -x: inside the cell, the next cell of the window, or the interface cell ox - 1
-    if (i % r)
-        site(s - 1);
-    else if (i > 0) {
-        if (grain[qs - 1] == g) site(s - 1);
-    } else if (ox > 0)
-        cell(qs - 1);
-    // +x
-    if ((i + 1) % r)
-        site(s + 1);
-    else if (i + 1 < P.nxw) {
-        if (grain[qs + 1] == g) site(s + 1);
-    } else if (ox + P.wx < P.ncx)
-        cell(qs + 1);
-    // -y, +y, -z, +z: open faces of the track
-    if (j % r)
-        site(s - sy);
-    else if (j > 0 && grain[qs - cy] == g)
-        site(s - sy);
-    if ((j + 1) % r)
-        site(s + sy);
-    else if (j + 1 < P.nyw && grain[qs + cy] == g)
-        site(s + sy);
-    if (k % r)
-        site(s - sz);
-    else if (k > 0 && grain[qs - cz] == g)
-        site(s - sz);
-    if ((k + 1) % r)
-        site(s + sz);
-    else if (k + 1 < P.nzw && grain[qs + cz] == g)
-        site(s + sz);
-    return {ex, ey, ez};
-}
-
 __device__ __forceinline__ float inv_norm(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
 
-template <typename Real, int RT>
-__global__ void k_ms_predict(const Real *S, Real *Sp, Real *F1, Real *BTH, const Real *m, const int *grain, MsDev P,
-                             ReplicaDev D, Field<Real> F, const Real *Bd, int ox, long long step) {
-    int i, j, k;
-    if (!coords(P.nxw, P.nyw, i, j, k)) return;
-    const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
-    const int qs = cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k));
-    const int g = grain[qs];
-    if (g < 0) {
-        Sp[s] = Sp[P.nw + s] = Sp[2 * P.nw + s] = Real(0);
-        return;
-    }
-    const Real t = (Real)step * (Real)P.dt, a = (Real)P.a;
-    const Real T = temp_at(D, ((Real)ox * P.r + i + Real(0.5)) * a, (j + Real(0.5)) * a, t);
-    const Real sig = (Real)P.sig0 * sqrt(T);
-    const unsigned long long X = (unsigned long long)ox * P.r + i, NX = (unsigned long long)P.ncx * P.r;
-    const unsigned long long site = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * k);
-    Real n0, n1, n2;
-    normals3(philox_site(P.key0, P.key1, site, (unsigned long long)step), n0, n1, n2);
-    const Real bthx = sig * n0, bthy = sig * n1, bthz = sig * n2;
-    BTH[s] = bthx;
-    BTH[P.nw + s] = bthy;
-    BTH[2 * P.nw + s] = bthz;
-    V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * a);
-    if (Bd) {   // the demagnetising field of the site's cell (Eq. 7)
-        ba.x += Bd[qs];
-        ba.y += Bd[P.nc + qs];
-        ba.z += Bd[2 * P.nc + qs];
-    }
-    const V3<Real> ex = exchange<Real, RT>(P, S, m, grain, ox, i, j, k, g, qs, s);
-    const Real Jm = (Real)P.J_mu, Km = (Real)P.ku2_mu;
-    const Real sx = S[s], sy = S[P.nw + s], sz = S[2 * P.nw + s];
-    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, sx, sy, sz, Jm * ex.x + ba.x + bthx,
-                                 Jm * ex.y + ba.y + bthy, Jm * ex.z + Km * sz + ba.z + bthz);
-    F1[s] = f.x;
-    F1[P.nw + s] = f.y;
-    F1[2 * P.nw + s] = f.z;
-    const Real dt = (Real)P.dt;
-    const Real vx = sx + dt * f.x, vy = sy + dt * f.y, vz = sz + dt * f.z;
-    const Real in = inv_norm(vx * vx + vy * vy + vz * vz);
-    Sp[s] = vx * in;
-    Sp[P.nw + s] = vy * in;
-    Sp[2 * P.nw + s] = vz * in;
-}
+// ---------------------------------------------------------------- fused window step
+// Both Heun stages of the window in one pass over its sites (Sec. II, Eq. 1-3): the predictor
+// S' = normalise(S + dt f(S)), the corrector normalise(S + dt/2 f(S) + dt/2 f(S')), both
+// with the same thermal field and the drivers at t_n.  A bond within a cell or across a cell
+// face between cells of one grain couples; across the window's x faces a site sees the cell
+// of the neighbour position, if that cell is of the site's grain.
+// A CTA takes a tile of MWX x MWY site columns and a range of MWZ planes.  Each of its threads
+// owns one column of the tile or of the two-column ring around it and marches up the planes
+// from the one below the range to the one above it: at plane k the tile and the inner ring
+// predict S'(k) (the outer ring only stages S for them), then, after the CTA's one barrier of
+// the step, the tile's threads correct plane k - 1.  The inner ring's S' is recomputed with
+// the same noise as the neighbouring tiles' (the counter is the site's track index), so no
+// CTA needs another's S'.  S and S' of the staged columns pass through shared memory as
+// (x, y, z, grain code) records; a column beyond the window's x face is the interface: its S
+// and S' are the direction m of the cell holding the neighbour position (frozen for the
+// window's step), its grain code that cell's.  Columns beyond the track's y edges, beyond the
+// track's ends and planes beyond its z faces read 0.
+constexpr int MWX = 28, MWY = 8, MWZ = 10;                        // tile columns, planes per item
+constexpr int MWSX = MWX + 4, MWSY = MWY + 4, MWPOS = MWSX * MWSY;  // staged columns: a warp per row
+constexpr int MWT = MWPOS;                                         // threads
+
+template <typename Real>
+struct V4 {
+    Real x, y, z, g;  // g: grain code (grain + 1, 0 for a non-magnetic site)
+};
 
 template <typename Real, int RT>
-__global__ void k_ms_correct(Real *S, const Real *Sp, const Real *F1, const Real *BTH, const Real *m, const int *grain,
-                             MsDev P, Field<Real> F, const Real *Bd, int ox, long long step) {
-    int i, j, k;
-    if (!coords(P.nxw, P.nyw, i, j, k)) return;
-    const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
-    const int qs = cell_at(P, ox + per_cell<RT>(P, i), per_cell<RT>(P, j), per_cell<RT>(P, k));
-    const int g = grain[qs];
-    if (g < 0) return;
-    const Real dt = (Real)P.dt;
-    V3<Real> ba = field_at(P, F, ((Real)ox * P.r + i + Real(0.5)) * (Real)P.a);
-    if (Bd) {
-        ba.x += Bd[qs];
-        ba.y += Bd[P.nc + qs];
-        ba.z += Bd[2 * P.nc + qs];
+__global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
+    k_ms_fused(const Real *__restrict__ Sin, Real *__restrict__ Sout, const Real *__restrict__ m,
+               const int *__restrict__ grain, MsDev P, ReplicaDev D, Field<Real> F, const Real *__restrict__ Bd,
+               int ox, long long step) {
+    extern __shared__ unsigned char ms_smem[];
+    V4<Real>(*sS)[MWPOS] = reinterpret_cast<V4<Real>(*)[MWPOS]>(ms_smem);  // [3]: S, plane k in slot k mod 3
+    V4<Real>(*sP)[MWPOS] = sS + 3;                                          // [4]: S', plane k in slot k mod 4
+    const int tid = threadIdx.x;
+    const bool own = tid < MWPOS;
+    const int ci = tid % MWSX, cj = tid / MWSX;
+    const int i = (int)blockIdx.x * MWX - 2 + ci, j = (int)blockIdx.y * MWY - 2 + cj;
+    const int z0 = (int)blockIdx.z * MWZ, z1 = min(P.nzw, z0 + MWZ);
+    const bool yin = j >= 0 && j < P.nyw;
+    const bool site = own && yin && i >= 0 && i < P.nxw;
+    // the interface cell column beyond the window's x face (-1: none)
+    int icx = -1;
+    if (own && yin && i == -1 && ox > 0) icx = ox - 1;
+    if (own && yin && i == P.nxw && ox + P.wx < P.ncx) icx = ox + P.wx;
+    const bool pred = ci >= 1 && ci <= MWX + 2 && cj >= 1 && cj <= MWY + 2;  // the tile and the inner ring
+    const bool inner = site && ci >= 2 && ci <= MWX + 1 && cj >= 2 && cj <= MWY + 1;
+    const int cy = yin ? per_cell<RT>(P, j) : 0;
+    const int cxs = site ? ox + per_cell<RT>(P, i) : 0;
+    const int lz = P.ncx * P.ncy;
+    // S and grain code of this column at plane k (0 off the window and off the track)
+    auto load = [&](int k, V4<Real> &v) {
+        v.x = v.y = v.z = v.g = Real(0);
+        if (k < 0 || k >= P.nzw) return;
+        if (site) {
+            const int gq = grain[cxs + P.ncx * cy + lz * per_cell<RT>(P, k)];
+            if (gq < 0) return;
+            const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
+            v.x = Sin[s];
+            v.y = Sin[P.nw + s];
+            v.z = Sin[2 * P.nw + s];
+            v.g = (Real)(gq + 1);
+        } else if (icx >= 0) {
+            const int q = icx + P.ncx * cy + lz * per_cell<RT>(P, k);
+            const int gq = grain[q];
+            if (gq < 0) return;
+            v.x = m[q];
+            v.y = m[P.nc + q];
+            v.z = m[2 * P.nc + q];
+            v.g = (Real)(gq + 1);
+        }
+    };
+    // per-column drivers: the laser's thermal-field scale and the applied field along x
+    const Real t = (Real)step * (Real)P.dt, a = (Real)P.a;
+    const Real xs = ((Real)ox * P.r + i + Real(0.5)) * a;
+    Real sig = 0;
+    V3<Real> ba0 = {0, 0, 0};
+    if (site) {
+        sig = (Real)P.sig0 * sqrt(temp_at(D, xs, (j + Real(0.5)) * a, t));
+        ba0 = field_at(P, F, xs);
     }
-    const V3<Real> ex = exchange<Real, RT>(P, Sp, m, grain, ox, i, j, k, g, qs, s);
-    const Real Jm = (Real)P.J_mu, Km = (Real)P.ku2_mu;
-    const Real px = Sp[s], py = Sp[P.nw + s], pz = Sp[2 * P.nw + s];
-    const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, px, py, pz, Jm * ex.x + ba.x + BTH[s],
-                                 Jm * ex.y + ba.y + BTH[P.nw + s], Jm * ex.z + Km * pz + ba.z + BTH[2 * P.nw + s]);
-    const Real vx = S[s] + Real(0.5) * dt * (F1[s] + f.x), vy = S[P.nw + s] + Real(0.5) * dt * (F1[P.nw + s] + f.y),
-               vz = S[2 * P.nw + s] + Real(0.5) * dt * (F1[2 * P.nw + s] + f.z);
-    const Real in = inv_norm(vx * vx + vy * vy + vz * vz);
-    S[s] = vx * in;
-    S[P.nw + s] = vy * in;
-    S[2 * P.nw + s] = vz * in;
+    const unsigned long long X = (unsigned long long)ox * P.r + (unsigned long long)(site ? i : 0),
+                             NX = (unsigned long long)P.ncx * P.r;
+    const Real Jm = (Real)P.J_mu, Km = (Real)P.ku2_mu, dt = (Real)P.dt, hdt = Real(0.5) * dt;
+
+    // prologue: S of planes z0 - 2 .. z0 in registers, plane z0 - 1 staged
+    V4<Real> m1, c0, p1, p2;
+    load(z0 - 2, m1);
+    load(z0 - 1, c0);
+    load(z0, p1);
+    if (own) sS[(z0 + 2) % 3][tid] = c0;
+    __syncthreads();
+    // the corrector base S + dt/2 f1 and the S-independent field (applied, thermal) of the
+    // plane awaiting correction; the own S' of planes k - 2 and k - 1
+    Real amx = 0, amy = 0, amz = 0, hmx = 0, hmy = 0, hmz = 0;
+    for (int k = z0 - 1; k <= z1; ++k) {
+        load(k + 2, p2);  // consumed two steps on: its latency overlaps this step
+        const int sk = (k + 3) % 3, pk = (k + 4) & 3;
+        // ---- predictor on plane k
+        V4<Real> sp = {0, 0, 0, 0};
+        Real anx = 0, any = 0, anz = 0, hx = 0, hy = 0, hz = 0;
+        if (icx >= 0) {
+            sp = c0;  // an interface cell: S' = m (frozen for the step)
+        } else if (site && pred && k >= 0 && k < P.nzw && c0.g != Real(0)) {
+            const unsigned long long sidx = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * k);
+            Real n0, n1, n2;
+            normals3(philox_site(P.key0, P.key1, sidx, (unsigned long long)step), n0, n1, n2);
+            V3<Real> ba = ba0;
+            if (Bd) {  // the demagnetising field of the site's cell (Eq. 7)
+                const int qs = cxs + P.ncx * cy + lz * per_cell<RT>(P, k);
+                ba.x += Bd[qs];
+                ba.y += Bd[P.nc + qs];
+                ba.z += Bd[2 * P.nc + qs];
+            }
+            hx = ba.x + sig * n0;
+            hy = ba.y + sig * n1;
+            hz = ba.z + sig * n2;
+            const V4<Real> *Q = sS[sk];
+            const Real g = c0.g;
+            Real ex = 0, ey = 0, ez = 0;
+            auto add = [&](const V4<Real> &v) {
+                if (v.g == g) {
+                    ex += v.x;
+                    ey += v.y;
+                    ez += v.z;
+                }
+            };
+            add(Q[tid - 1]);
+            add(Q[tid + 1]);
+            add(Q[tid - MWSX]);
+            add(Q[tid + MWSX]);
+            add(m1);
+            add(p1);
+            const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, c0.x, c0.y, c0.z, Jm * ex + hx, Jm * ey + hy,
+                                         Jm * ez + Km * c0.z + hz);
+            anx = c0.x + hdt * f.x;
+            any = c0.y + hdt * f.y;
+            anz = c0.z + hdt * f.z;
+            const Real vx = c0.x + dt * f.x, vy = c0.y + dt * f.y, vz = c0.z + dt * f.z;
+            const Real in = inv_norm(vx * vx + vy * vy + vz * vz);
+            sp = {vx * in, vy * in, vz * in, g};
+        }
+        if (own) {
+            sP[pk][tid] = sp;
+            sS[(k + 4) % 3][tid] = p1;  // S of plane k + 1, read by the next step's predictor
+        }
+        __syncthreads();
+        // ---- corrector on plane k - 1 (the tile's columns)
+        const int kc = k - 1;
+        if (inner && kc >= z0 && kc < z1) {
+            const V4<Real> *Q = sP[(kc + 4) & 3];
+            const V4<Real> v = Q[tid];
+            const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * kc);
+            Real ox_ = 0, oy_ = 0, oz_ = 0;
+            if (v.g != Real(0)) {
+                const Real g = v.g;
+                Real ex = 0, ey = 0, ez = 0;
+                auto add = [&](const V4<Real> &w) {
+                    if (w.g == g) {
+                        ex += w.x;
+                        ey += w.y;
+                        ez += w.z;
+                    }
+                };
+                add(Q[tid - 1]);
+                add(Q[tid + 1]);
+                add(Q[tid - MWSX]);
+                add(Q[tid + MWSX]);
+                add(sP[(kc + 3) & 3][tid]);  // S'(k - 2), own
+                add(sp);                     // S'(k), own
+                const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, v.x, v.y, v.z, Jm * ex + hmx,
+                                             Jm * ey + hmy, Jm * ez + Km * v.z + hmz);
+                const Real wx = amx + hdt * f.x, wy = amy + hdt * f.y, wz = amz + hdt * f.z;
+                const Real in = inv_norm(wx * wx + wy * wy + wz * wz);
+                ox_ = wx * in;
+                oy_ = wy * in;
+                oz_ = wz * in;
+            }
+            Sout[s] = ox_;
+            Sout[P.nw + s] = oy_;
+            Sout[2 * P.nw + s] = oz_;
+        }
+        m1 = c0;
+        c0 = p1;
+        p1 = p2;
+        amx = anx;
+        amy = any;
+        amz = anz;
+        hmx = hx;
+        hmy = hy;
+        hmz = hz;
+    }
 }
 
 // Per column (cx, cy) of magnetic cells at time t (FP64): the laser temperature at the column's
@@ -750,9 +815,9 @@ struct hamr_ms_ctx {
     int *grain_d = nullptr;
     std::vector<int> grain_h;
     int prec = HAMR_FP64;         // arithmetic of the state and the field (HAMR_FP32 / HAMR_FP64)
-    // state-precision planes: cells m, V0, V1, acc, coef [3][nc]; window S, S2, Sp, F1, BTH [3][nw]
+    // state-precision planes: cells m, V0, V1, acc, coef [3][nc]; window S, S2 [3][nw]
     void *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *coef = nullptr;
-    void *S = nullptr, *S2 = nullptr, *Sp = nullptr, *F1 = nullptr, *BTH = nullptr;
+    void *S = nullptr, *S2 = nullptr;
     void *wn = nullptr;           // |sum of the sites| of each window cell (Eq. 6), state precision
     double *me = nullptr;         // m_e per cell (FP64)
     double *me_prev = nullptr;    // m_e of each cell's solve before the last one (NaN: none)
@@ -813,7 +878,7 @@ struct MsDeviceGuard {
 };
 
 void ms_free(hamr_ms_t h) {
-    void **bufs[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef, &h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
+    void **bufs[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef, &h->S, &h->S2};
     for (void **b : bufs)
         if (*b) {
             cudaFree(*b);
@@ -1162,7 +1227,7 @@ int ms_step(hamr_ms_t h) {
     cudaStream_t st = h->stream;
     int rc = ms_average<Real>(h, h->ox, P.wx);
     if (rc) return rc;
-    Real *S = (Real *)h->S, *Sp = (Real *)h->Sp, *F1 = (Real *)h->F1, *BTH = (Real *)h->BTH, *m = (Real *)h->m;
+    Real *S = (Real *)h->S, *m = (Real *)h->m;
     const double t = (double)h->step * P.dt;
     const Field<Real> F = field_of<Real>(h, t);
     // m_e(T) at t_n of every cell of the simulated region (frozen cells keep theirs), then
@@ -1180,11 +1245,16 @@ int ms_step(hamr_ms_t h) {
         if ((rc = ms_demag_step<Real>(h))) return rc;
         Bd = (const Real *)h->Bd;
     }
-    const dim3 gw = grid3(P.nxw, P.nyw, P.nzw);
-#define MS_HEUN(RT)                                                                                              \
-    do {                                                                                                         \
-        k_ms_predict<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, h->D, F, Bd, h->ox, h->step); \
-        k_ms_correct<Real, RT><<<gw, BLK3, 0, st>>>(S, Sp, F1, BTH, m, h->grain_d, P, F, Bd, h->ox, h->step);       \
+    // both Heun stages of the window in one pass, into the second buffer
+    const dim3 gw((unsigned)((P.nxw + MWX - 1) / MWX), (unsigned)((P.nyw + MWY - 1) / MWY),
+                  (unsigned)((P.nzw + MWZ - 1) / MWZ));
+    const size_t shm = sizeof(V4<Real>) * 7 * MWPOS;
+#define MS_HEUN(RT)                                                                                         \
+    do {                                                                                                    \
+        MSCK(h, cudaFuncSetAttribute(k_ms_fused<Real, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                     (int)shm));                                                           \
+        k_ms_fused<Real, RT><<<gw, MWT, shm, st>>>(S, (Real *)h->S2, m, h->grain_d, P, h->D, F, Bd, h->ox, \
+                                                   h->step);                                               \
     } while (0)
     switch (P.r) {
         case 1: MS_HEUN(1); break;
@@ -1194,6 +1264,7 @@ int ms_step(hamr_ms_t h) {
     }
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
+    std::swap(h->S, h->S2);
     const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
     for (int s = 0; s < 4; ++s) {
         const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
@@ -1316,7 +1387,7 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me_prev, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->Tq, sizeof(double) * nc);
-    void **bufs3w[] = {&h->S, &h->S2, &h->Sp, &h->F1, &h->BTH};
+    void **bufs3w[] = {&h->S, &h->S2};
     for (void **b : bufs3w)
         if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nw);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->stage, sizeof(double) * 3 * (nw > nc ? nw : nc));
