@@ -262,7 +262,7 @@ __device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
 // and S' are the direction m of the cell holding the neighbour position (frozen for the
 // window's step), its grain code that cell's.  Columns beyond the track's y edges, beyond the
 // track's ends and planes beyond its z faces read 0.
-constexpr int MWX = 28, MWY = 8, MWZ = 10;                        // tile columns, planes per item
+constexpr int MWX = 28, MWY = 8, MWZ = 40;                        // tile columns, planes per item
 constexpr int MWSX = MWX + 4, MWSY = MWY + 4, MWPOS = MWSX * MWSY;  // staged columns: a warp per row
 constexpr int MWT = MWPOS;                                         // threads
 
@@ -441,47 +441,47 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
 
 // Per column (cx, cy) of magnetic cells at time t (FP64): the laser temperature at the column's
 // centre and the write field depend on (x, y) only, so every cell of the column has the same
-// m_e(T, |B_app|), solved once.  Newton starts from 2 m_e - m_e' (m_e and m_e' the last two
-// solves of the column's first magnetic cell; m_e alone when that leaves (0, 1] or there is no
-// m_e'): the changes from step to step are smooth, so the first Newton step is usually already
-// below the convergence bound.  Every magnetic cell of the column then gets m_e, its history
-// and its field and damping coefficients 2 A(T)/Ms(T) = 2 A0 m_e / Ms0,
-// 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0, alpha = lambda (1 - T/3T_C) with T held in [0, T_C],
-// stored in the arithmetic of the state.  A column whose cells all solved last at this
-// temperature and field magnitude (Bm == Bm_last, T == Tq) keeps its values: far from the
-// spot T is the ambient temperature to the last bit.
+// m_e(T, |B_app|), solved once.  The column keeps its solve state in col [3][ncx ncy]: the
+// temperature of its last solve (NaN: none), m_e and the m_e before it (NaN: none).  Newton
+// starts from 2 m_e - m_e' (m_e alone when that leaves (0, 1] or there is no m_e'): the changes
+// from step to step are smooth, so the first Newton step is usually already below the
+// convergence bound.  A column solved last at this temperature and field magnitude
+// (Bm == Bm_last, T unchanged) keeps its values: far from the spot T is the ambient
+// temperature to the last bit.  Otherwise every magnetic cell of the column (bit z of the
+// column's mask; planes from 64 on look up their grain) gets m_e and its field and damping
+// coefficients 2 A(T)/Ms(T) = 2 A0 m_e / Ms0, 2 K(T)/Ms(T) = 2 K0 m_e^2 / Ms0,
+// alpha = lambda (1 - T/3T_C) with T held in [0, T_C], stored in the arithmetic of the
+// state.  The thread's loads are independent of one another and its cell writes are stores
+// only: with one thread per column the launch is short of warps, so chains of dependent loads
+// would set its duration.
 template <typename Real>
-__global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, const int *grain, MsDev P,
-                          ReplicaDev D, double t, Field<double> F, double Bm_last, int cx0, int ncol) {
+__global__ void k_mm_prep(double *me, double *col, Real *coef, const int *grain, const unsigned long long *colmask,
+                          MsDev P, ReplicaDev D, double t, Field<double> F, double Bm_last, int cx0, int ncol) {
     int cx, cy, cz;
     if (!coords(ncol, P.ncy, cx, cy, cz)) return;
     cx += cx0;
-    const int q0 = cell_at(P, cx, cy, 0), lz = P.ncx * P.ncy;
+    const int lz = P.ncx * P.ncy, c = cx + P.ncx * cy;
+    const unsigned long long msk = colmask[c];
+    const double Tl = col[c], e0 = col[lz + c], ep = col[2 * lz + c];
     const double T = temperature(D, (cx + 0.5) * P.cell, (cy + 0.5) * P.cell, t);
     const V3<double> B = field_at(P, F, (cx + 0.5) * P.cell);
     const double Bm = sqrt(B.x * B.x + B.y * B.y + B.z * B.z);
-    int first = -1;
-    bool same = !P.profile && Bm == Bm_last;
-    for (int z = 0; z < P.ncz; ++z) {
-        const int q = q0 + z * lz;
-        if (grain[q] < 0) continue;
-        if (first < 0) first = q;
-        same = same && T == Tq[q];
-    }
-    if (first < 0 || same) return;
-    const double e0 = me[first], ep = me_prev[first];
+    bool any = msk != 0;
+    for (int z = 64; z < P.ncz && !any; ++z) any = grain[c + z * lz] >= 0;
+    if (!any || (!P.profile && Bm == Bm_last && T == Tl)) return;
     double m0 = 2.0 * e0 - ep;
     if (!(m0 > 0.0 && m0 <= 1.0)) m0 = e0;
     const double e = me_root(P.T_C, T, P.mu_kB, Bm, m0);
+    col[c] = T;
+    col[lz + c] = e;
+    col[2 * lz + c] = e0;
     double cex = P.cA * e, cK = P.cK * e * e;
     if (!(e > 0.0)) cex = cK = 0.0;
     const double Tc = fmax(fmin(T, P.T_C), 0.0);
     const Real rex = (Real)cex, rK = (Real)cK, ral = (Real)(P.lambda * (1.0 - Tc * P.i3TC));
     for (int z = 0; z < P.ncz; ++z) {
-        const int q = q0 + z * lz;
-        if (grain[q] < 0) continue;
-        Tq[q] = T;
-        me_prev[q] = me[q];
+        const int q = c + z * lz;
+        if (z < 64 ? !((msk >> z) & 1ull) : grain[q] < 0) continue;
         me[q] = e;
         coef[q] = rex;
         coef[P.nc + q] = rK;
@@ -493,10 +493,9 @@ __global__ void k_mm_prep(double *me, double *me_prev, double *Tq, Real *coef, c
 // window: K = dm/dt at the stage values Vin, acc += w K and Vout = m + c dt K (the next
 // stage's values).  A window cell, and a frozen cell next to the simulated region, writes its
 // m to Vout, so that every stage buffer holds m there (stage 0 reads m itself); the launch
-// covers [e0, e1), one column beyond the region on each side.  Non-magnetic cells are never
-// read.  The cell's grain code, its stage value and its neighbours' grain
-// codes are loaded together before the tests: the threads are short and bound by memory
-// latency.
+// covers [e0, e1), one column beyond the region on each side.  The values of non-magnetic
+// cells are never used (they may be unset).  The threads are short and bound by memory
+// latency, so every value a thread may need is loaded before any test.
 template <typename Real>
 __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
                            MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first, int e0, int ne,
@@ -505,17 +504,33 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     if (!coords(ne, P.ncy, cx, cy, cz)) return;
     cx += e0;
     const int q = cell_at(P, cx, cy, cz), lz = P.ncx * P.ncy;
-    const int g = grain[q];
-    const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
-    // neighbours -x, +x, -y, +y, -z, +z (an absent one reads the cell itself and is masked)
+    // neighbours -x, +x, -y, +y, -z, +z (an absent one reads the cell itself and is masked).
+    // Every load below is of a valid address and none waits on a test: one round trip.
     const bool has[6] = {cx > 0, cx + 1 < P.ncx, cy > 0, cy + 1 < P.ncy, cz > 0, cz + 1 < P.ncz};
     const int qn[6] = {has[0] ? q - 1 : q, has[1] ? q + 1 : q, has[2] ? q - P.ncx : q,
                        has[3] ? q + P.ncx : q, has[4] ? q - lz : q, has[5] ? q + lz : q};
+    const int g = grain[q];
     int gn[6];
+    Real nx[6], ny[6], nz[6];
 #pragma unroll
-    for (int b = 0; b < 6; ++b) gn[b] = grain[qn[b]];
-    if (g < 0) return;
+    for (int b = 0; b < 6; ++b) {
+        gn[b] = grain[qn[b]];
+        nx[b] = Vin[qn[b]];
+        ny[b] = Vin[P.nc + qn[b]];
+        nz[b] = Vin[2 * P.nc + qn[b]];
+    }
+    const Real vx = Vin[q], vy = Vin[P.nc + q], vz = Vin[2 * P.nc + q];
     const Real mx = m[q], my = m[P.nc + q], mz = m[2 * P.nc + q];
+    const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
+    const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
+               a2 = first ? Real(0) : acc[2 * P.nc + q];
+    Real bx = 0, by = 0, bz = 0;
+    if (Bd) {
+        bx = Bd[q];
+        by = Bd[P.nc + q];
+        bz = Bd[2 * P.nc + q];
+    }
+    if (g < 0) return;
     if ((cx >= ox && cx < ox + P.wx) || cx < c0 || cx >= c1) {  // a window or frozen cell: not evolved here
         Vout[q] = mx;
         Vout[P.nc + q] = my;
@@ -525,26 +540,20 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     Real lx = 0, ly = 0, lz2 = 0;
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
-        if (!has[b] || gn[b] != g) continue;
-        lx += Vin[qn[b]] - vx;
-        ly += Vin[P.nc + qn[b]] - vy;
-        lz2 += Vin[2 * P.nc + qn[b]] - vz;
+        const bool on = has[b] && gn[b] == g;  // a select: a non-magnetic neighbour's values are never used
+        lx += on ? nx[b] - vx : Real(0);
+        ly += on ? ny[b] - vy : Real(0);
+        lz2 += on ? nz[b] - vz : Real(0);
     }
     const Real ic2 = (Real)(1.0 / (P.cell * P.cell));
     lx *= ic2;
     ly *= ic2;
     lz2 *= ic2;
-    const Real cex = coef[q], cK = coef[P.nc + q], alpha = coef[2 * P.nc + q];
     const V3<Real> ba = field_at(P, F, (Real)((cx + 0.5) * P.cell));
-    Real bx = ba.x, by = ba.y, bz = ba.z;
-    if (Bd) {
-        bx += Bd[q];
-        by += Bd[P.nc + q];
-        bz += Bd[2 * P.nc + q];
-    }
+    bx += ba.x;
+    by += ba.y;
+    bz += ba.z;
     const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz2 + cK * vz + bz);
-    const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
-               a2 = first ? Real(0) : acc[2 * P.nc + q];
     acc[q] = a0 + w * k.x;
     acc[P.nc + q] = a1 + w * k.y;
     acc[2 * P.nc + q] = a2 + w * k.z;
@@ -814,14 +823,15 @@ struct hamr_ms_ctx {
     uint8_t *bits_d = nullptr;
     int *grain_d = nullptr;
     std::vector<int> grain_h;
+    std::vector<unsigned long long> colmask_h;
     int prec = HAMR_FP64;         // arithmetic of the state and the field (HAMR_FP32 / HAMR_FP64)
     // state-precision planes: cells m, V0, V1, acc, coef [3][nc]; window S, S2 [3][nw]
     void *m = nullptr, *V0 = nullptr, *V1 = nullptr, *acc = nullptr, *coef = nullptr;
     void *S = nullptr, *S2 = nullptr;
     void *wn = nullptr;           // |sum of the sites| of each window cell (Eq. 6), state precision
     double *me = nullptr;         // m_e per cell (FP64)
-    double *me_prev = nullptr;    // m_e of each cell's solve before the last one (NaN: none)
-    double *Tq = nullptr;         // temperature of each cell's last m_e solve (NaN: none)
+    double *col = nullptr;        // per cell column [3][ncx ncy]: T of the last m_e solve, m_e, the m_e before (NaN: none)
+    unsigned long long *colmask = nullptr;  // per cell column: bit z set for a magnetic cell (z < 64)
     double Bm_last = NAN;         // field magnitude of the last m_e solve
     double *stage = nullptr;      // AoS FP64 staging for host copies
     int ox = -1;                  // window column (-1: not placed)
@@ -894,13 +904,13 @@ void ms_free(hamr_ms_t h) {
     demag_grid_free(h->gregion);
     if (h->wn) cudaFree(h->wn);
     if (h->me) cudaFree(h->me);
-    if (h->me_prev) cudaFree(h->me_prev);
-    if (h->Tq) cudaFree(h->Tq);
+    if (h->col) cudaFree(h->col);
+    if (h->colmask) cudaFree(h->colmask);
     if (h->stage) cudaFree(h->stage);
     h->wn = nullptr;
     h->me = nullptr;
-    h->me_prev = nullptr;
-    h->Tq = nullptr;
+    h->col = nullptr;
+    h->colmask = nullptr;
     h->stage = nullptr;
     if (h->grain_d) cudaFree(h->grain_d);
     if (h->bits_d) cudaFree(h->bits_d);
@@ -1179,8 +1189,8 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t, bool all) {
     if (!all) ms_region(h, c0, c1);
     const double Bm = field_magnitude_host(h, t);
     k_mm_prep<Real><<<grid3(c1 - c0, h->P.ncy, 1), BLK3, 0, h->stream>>>(
-        h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, h->P, h->D, t, field_of<double>(h, t), h->Bm_last, c0,
-        c1 - c0);
+        h->me, h->col, (Real *)h->coef, h->grain_d, h->colmask, h->P, h->D, t, field_of<double>(h, t), h->Bm_last,
+        c0, c1 - c0);
     h->Bm_last = Bm;
     k_ms_thermalise<Real><<<nblk(n), BLK, 0, h->stream>>>((Real *)h->S, (const Real *)h->m, h->me, h->grain_d, h->P,
                                                           h->ox, cx0, cx1, (unsigned long long)h->events);
@@ -1236,7 +1246,7 @@ int ms_step(hamr_ms_t h) {
     ms_region(h, c0, c1);
     const int e0 = std::max(0, c0 - 1), e1 = std::min(P.ncx, c1 + 1);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<grid3(c1 - c0, P.ncy, 1), BLK3, 0, st>>>(h->me, h->me_prev, h->Tq, (Real *)h->coef, h->grain_d, P,
+    k_mm_prep<Real><<<grid3(c1 - c0, P.ncy, 1), BLK3, 0, st>>>(h->me, h->col, (Real *)h->coef, h->grain_d, h->colmask, P,
                                                               h->D, t, field_of<double>(h, t), h->Bm_last, c0, c1 - c0);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
@@ -1385,8 +1395,10 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
         if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nc);
     if (e == cudaSuccess) e = cudaMalloc(&h->wn, el * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->me, sizeof(double) * nc);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->me_prev, sizeof(double) * nc);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->Tq, sizeof(double) * nc);
+    const long long ncol = (long long)h->P.ncx * h->P.ncy;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->col, sizeof(double) * 3 * ncol);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->colmask, sizeof(unsigned long long) * ncol);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->colmask, 0, sizeof(unsigned long long) * ncol, h->stream);
     void **bufs3w[] = {&h->S, &h->S2};
     for (void **b : bufs3w)
         if (e == cudaSuccess) e = cudaMalloc(b, el * 3 * nw);
@@ -1398,8 +1410,9 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->grain_d, 0, sizeof(int) * nc, h->stream);
     if (e == cudaSuccess) {
         k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->me, 1.0, nc);
-        k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->me_prev, NAN, nc);
-        k_fill<<<nblk(nc), BLK, 0, h->stream>>>(h->Tq, NAN, nc);
+        k_fill<<<nblk(ncol), BLK, 0, h->stream>>>(h->col, NAN, ncol);
+        k_fill<<<nblk(ncol), BLK, 0, h->stream>>>(h->col + ncol, 1.0, ncol);
+        k_fill<<<nblk(ncol), BLK, 0, h->stream>>>(h->col + 2 * ncol, NAN, ncol);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1422,6 +1435,17 @@ int hamr_ms_set_grain_map(hamr_ms_t h, const int32_t *cell_grain) {
     MsDeviceGuard dg(h->device);
     h->grain_h.assign(cell_grain, cell_grain + h->P.nc);
     MSCK(h, cudaMemcpyAsync(h->grain_d, h->grain_h.data(), sizeof(int) * h->P.nc, cudaMemcpyHostToDevice, h->stream));
+    // the magnetic planes of every cell column, and no column's m_e solve kept: cells that
+    // turned magnetic get theirs at the next solve
+    const long long ncol = (long long)h->P.ncx * h->P.ncy;
+    h->colmask_h.assign(ncol, 0ull);
+    for (int z = 0; z < h->P.ncz && z < 64; ++z)
+        for (long long c = 0; c < ncol; ++c)
+            if (cell_grain[c + ncol * z] >= 0) h->colmask_h[c] |= 1ull << z;
+    MSCK(h, cudaMemcpyAsync(h->colmask, h->colmask_h.data(), sizeof(unsigned long long) * ncol, cudaMemcpyHostToDevice,
+                            h->stream));
+    k_fill<<<nblk(ncol), BLK, 0, h->stream>>>(h->col, NAN, ncol);
+    MSCK(h, cudaGetLastError());
     int rc = ms_zero_void(h);
     if (rc) return rc;
     MSCK(h, cudaStreamSynchronize(h->stream));
