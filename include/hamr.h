@@ -370,10 +370,18 @@ int hamr_ms_set_region(hamr_ms_t h, int32_t margin);
  * Res. 98, 9551 (1993); the point-dipole tensor beyond 40 cell edges), M = Ms0 m_e(T) m on
  * micromagnetic cells and M = (mu_s / V) sum of its spins on window cells (Eq. 6, Sec. II),
  * recomputed every step from the state at t_n and added to the field of every cell and of
- * every site in it.  Convolution by FFT on a zero-padded grid (cuFFT); the first call with
- * on != 0 builds the tensor (host, FP64) and its transform.  on = 0 switches it off.
+ * every site in it.  The convolution: in x and y by FFT on a grid zero-padded to twice the
+ * columns and rows (cuFFT, one in-plane transform per plane and component), along z by the
+ * direct sum over the track's planes at every in-plane frequency; the first call with
+ * on != 0 builds the tensor (host, FP64) and its transforms.  on = 0 switches it off.
  * Errors: OOM, CUDA. */
 int hamr_ms_set_demag(hamr_ms_t h, int32_t on);
+/* B_d = -mu0 N * M (Eq. 7, the convolution of hamr_ms_set_demag over the whole track) for a
+ * given magnetisation M [A/m] of every cell (3 ncx ncy ncz doubles, AoS, non-magnetic cells
+ * included; read only) into B_out [T] (same layout, caller-owned), computed in the handle's
+ * precision.  The state is not touched.  ARG on NULL or non-finite M, STATE while Eq. 7 is
+ * off (hamr_ms_set_demag(h, 1) first), CUDA on a failed transform. */
+int hamr_ms_demag_field(hamr_ms_t h, const double *M, double *B_out);
 /* Micromagnetic directions m (3 ncx ncy ncz doubles, AoS; copied; non-magnetic cells are
  * set to 0).  ARG on non-finite values. */
 int hamr_ms_set_cells(hamr_ms_t h, const double *m);

@@ -695,10 +695,15 @@ __global__ void k_ms_read_track(const Real *m, const int *grain, MsDev P, double
     if (threadIdx.x == 0) signal[b] = scnt[0] > 0 ? ssum[0] / (double)scnt[0] : 0.0;
 }
 
-// ---- demagnetising field (Eq. 7) by FFT convolution on a zero-padded grid Px x Py x Pz
+// ---- demagnetising field (Eq. 7): in x and y an FFT convolution on a zero-padded grid
+// Px x Py, along z (a few cells) the direct sum over the planes: for every in-plane frequency
+// (kx, ky), H^(t) = sum over planes z' of N^(t - z') M^(z'), N^(d) the in-plane transform of
+// the tensor at z offset d.  The same convolution as a 3-D transform padded along z, with
+// half the transformed points and no transform along z.
 struct Pad {
-    int Px, Py, Pz;
-    long long Ptot, Pc;   // real points, complex points (Px / 2 + 1 along x)
+    int Px, Py, Pz;       // padded x, y; Pz = the track's planes (not padded)
+    long long Ptot, Pc;   // real points, complex points (Px / 2 + 1 along x), all planes
+    long long Pc2;        // complex points of one plane
 };
 
 // The cells' magnetisation in the padded layout of a grid whose first column is g0 (ncol
@@ -706,17 +711,23 @@ struct Pad {
 // and m its direction, from the window average of the same state), other magnetic cells
 // M = Ms0 m_e m (a frozen cell's m_e is the stored one), non-magnetic cells and columns beyond
 // the track 0.  mode selects the sources: 0 every cell, 1 the columns [s0, s1) only, 2 all
-// but those.
+// but those, 3 the magnetisation Mg [3][nc] given for every cell.
 template <typename Real>
 __global__ void k_demag_M(Real *Mpad, const Real *wn, const Real *m, const double *me, const int *grain, MsDev P,
-                          Pad pd, int ox, int g0, int ncol, int s0, int s1, int mode) {
+                          Pad pd, int ox, int g0, int ncol, int s0, int s1, int mode, const Real *Mg) {
     int i, cy, cz;
     if (!coords(ncol, P.ncy, i, cy, cz)) return;
     const int cx = g0 + i;
     const long long pp = i + (long long)pd.Px * (cy + (long long)pd.Py * cz);
     Real Mx = 0, My = 0, Mz = 0;
     const int q = cx < P.ncx ? cell_at(P, cx, cy, cz) : 0;
-    if (cx < P.ncx && grain[q] >= 0 && (mode == 0 || (mode == 1) == (cx >= s0 && cx < s1))) {
+    if (mode == 3) {
+        if (cx < P.ncx) {
+            Mx = Mg[q];
+            My = Mg[P.nc + q];
+            Mz = Mg[2 * P.nc + q];
+        }
+    } else if (cx < P.ncx && grain[q] >= 0 && (mode == 0 || (mode == 1) == (cx >= s0 && cx < s1))) {
         // a window cell: (mu_s / V) |sum of its sites| times their direction, both from Eq. 6
         // of this step; a cell outside: Ms0 m_e(T) m
         const Real a = (cx >= ox && cx < ox + P.wx) ? (Real)(P.mu_s / (P.cell * P.cell * P.cell)) * wn[q]
@@ -730,33 +741,124 @@ __global__ void k_demag_M(Real *Mpad, const Real *wn, const Real *m, const doubl
     Mpad[2 * pd.Ptot + pp] = Mz;
 }
 
-// H^ = N^ M^ at every frequency (N symmetric: xx, yy, zz, xy, xz, yz)
-template <typename C>
-__global__ void k_demag_multiply(C *Mh, const C *Nh, long long Pc) {
+// The in-plane transform of each tensor component is real or imaginary: on the padded grid
+// xx, yy, zz are even in x and in y, xy odd in both (real transforms), xz odd in x and even in
+// y, yz the reverse (imaginary).  N^ is kept as one real per component: the real part of xx,
+// yy, zz, xy, the imaginary part of xz, yz.
+// h += N m for the tensor r at z offset +d (neg = false) or -d (neg = true: N is even in z
+// but for xz and yz, which are odd)
+template <typename C, typename R>
+__device__ __forceinline__ void tmac(C h[3], const R r[6], const C m[3], bool neg) {
+    auto re = [](C &a, R c, const C &b) {  // a += c b
+        a.x += c * b.x;
+        a.y += c * b.y;
+    };
+    auto im = [](C &a, R c, const C &b) {  // a += (i c) b
+        a.x -= c * b.y;
+        a.y += c * b.x;
+    };
+    const R xz = neg ? -r[4] : r[4], yz = neg ? -r[5] : r[5];
+    re(h[0], r[0], m[0]);
+    re(h[0], r[3], m[1]);
+    im(h[0], xz, m[2]);
+    re(h[1], r[3], m[0]);
+    re(h[1], r[1], m[1]);
+    im(h[1], yz, m[2]);
+    im(h[2], xz, m[0]);
+    im(h[2], yz, m[1]);
+    re(h[2], r[2], m[2]);
+}
+
+// The compressed tensor [6][Pz][Pc2] from its full in-plane transforms Nc [6][Pz][Pc2].
+template <typename C, typename R>
+__global__ void k_demag_tensor_compress(R *Nr, const C *Nc, long long Pc) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= 6 * Pc) return;
+    Nr[k] = k < 4 * Pc ? Nc[k].x : Nc[k].y;
+}
+
+// H^ [3][Pz][Pc2] from M^ [3][Pz][Pc2] and N^ [6][Pz][Pc2] (offsets 0 .. Pz - 1): one thread
+// per in-plane frequency and target plane t, summing over the source planes.
+template <typename C, typename R>
+__global__ void k_demag_zmul(C *Hh, const C *Mh, const R *Nr, long long Pc2, int Pz) {
     const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f >= Pc) return;
-    const C mx = Mh[f], my = Mh[Pc + f], mz = Mh[2 * Pc + f];
-    const C nxx = Nh[f], nyy = Nh[Pc + f], nzz = Nh[2 * Pc + f], nxy = Nh[3 * Pc + f], nxz = Nh[4 * Pc + f],
-            nyz = Nh[5 * Pc + f];
-    auto mul = [](C a, C b) {
-        C r;
-        r.x = a.x * b.x - a.y * b.y;
-        r.y = a.x * b.y + a.y * b.x;
-        return r;
-    };
-    auto add3 = [](C a, C b, C c) {
-        C r;
-        r.x = a.x + b.x + c.x;
-        r.y = a.y + b.y + c.y;
-        return r;
-    };
-    Mh[f] = add3(mul(nxx, mx), mul(nxy, my), mul(nxz, mz));
-    Mh[Pc + f] = add3(mul(nxy, mx), mul(nyy, my), mul(nyz, mz));
-    Mh[2 * Pc + f] = add3(mul(nxz, mx), mul(nyz, my), mul(nzz, mz));
+    const int t = blockIdx.y;
+    if (f >= Pc2) return;
+    const long long Pc = Pc2 * Pz;
+    C h[3];
+    for (int c = 0; c < 3; ++c) h[c].x = h[c].y = 0;
+    for (int z = 0; z < Pz; ++z) {
+        const int d = t - z, ad = d < 0 ? -d : d;
+        R n[6];
+        C m[3];
+        for (int c = 0; c < 6; ++c) n[c] = Nr[c * Pc + ad * Pc2 + f];
+        for (int c = 0; c < 3; ++c) m[c] = Mh[c * Pc + z * Pc2 + f];
+        tmac(h, n, m, d < 0);
+    }
+    for (int c = 0; c < 3; ++c) Hh[c * Pc + t * Pc2 + f] = h[c];
+}
+
+// global -> shared copies that hold no register while in flight, and the wait for all of the
+// calling thread's copies
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The same in FP32 for NZ planes (a compile-time count).  A block takes 32 frequencies; its
+// NP = min(NZ, 4) parts split the target planes (part p: t = p, p + NP, ...), so that a small
+// grid still has several warps per scheduler.  The block stages M^ and N^ of its
+// frequencies in shared memory (copies all in flight at once, one barrier); each thread holds
+// the NZ source vectors in registers and reads each tensor value where a pair needs it.
+template <int NZ>
+__global__ void __launch_bounds__(32 * (NZ < 4 ? NZ : 4))
+    k_demag_zmul_r(float2 *Hh, const float2 *Mh, const float *Nr, long long Pc2) {
+    constexpr int NP = NZ < 4 ? NZ : 4;
+    __shared__ float2 sM[3 * NZ][32];
+    __shared__ float sN[6 * NZ][32];
+    const int tx = threadIdx.x, p = threadIdx.y;
+    const long long f = blockIdx.x * 32LL + tx;
+    const bool act = f < Pc2;
+    const long long Pc = Pc2 * NZ;
+    if (act) {
+        for (int k = p; k < 3 * NZ; k += NP) cp_async8(&sM[k][tx], &Mh[k * Pc2 + f]);
+        for (int k = p; k < 6 * NZ; k += NP) cp_async4(&sN[k][tx], &Nr[k * Pc2 + f]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!act) return;
+    float2 m[NZ][3];
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m[z][c] = sM[c * NZ + z][tx];
+#pragma unroll
+    for (int t0 = 0; t0 < NZ; t0 += NP) {
+        const int t = t0 + p;
+        if (t >= NZ) break;
+        float2 h[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c].x = h[c].y = 0.f;
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) {
+            const int d = t - z, ad = d < 0 ? -d : d;
+            float r[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) r[c] = sN[c * NZ + ad][tx];
+            tmac(h, r, m[z], d < 0);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Hh[c * Pc + t * Pc2 + f] = h[c];
+    }
 }
 
 // B_d = -mu0 H on the cells of the target columns [t0, t1) of a grid whose first column is g0
-// (the inverse transform is unnormalised: divide by Ptot), plus `add` where given.
+// (the inverse in-plane transform is unnormalised: divide by Px Py), plus `add` where given.
 template <typename Real>
 __global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd, int g0, int ncol, int t0, int t1,
                                 const Real *add) {
@@ -766,7 +868,7 @@ __global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd, int
     if (cx < t0 || cx >= t1 || cx >= P.ncx) return;
     const int q = cell_at(P, cx, cy, cz);
     const long long pp = i + (long long)pd.Px * (cy + (long long)pd.Py * cz);
-    const Real s = (Real)(-1.25663706212e-6 / (double)pd.Ptot);
+    const Real s = (Real)(-1.25663706212e-6 / ((double)pd.Px * pd.Py));
     Real bx = s * Hpad[pp], by = s * Hpad[pd.Ptot + pp], bz = s * Hpad[2 * pd.Ptot + pp];
     if (add) {
         bx += add[q];
@@ -778,9 +880,9 @@ __global__ void k_demag_extract(Real *Bd, const Real *Hpad, MsDev P, Pad pd, int
     Bd[2 * P.nc + q] = bz;
 }
 
-// One zero-padded convolution grid of Eq. 7 over ncol cell columns (all of y and z): the
-// tensor's spectra [6][Pc], the padded M | H buffer [6][Ptot], the transformed M [3][Pc] and
-// the cuFFT plans (three transforms per call).
+// One convolution grid of Eq. 7 over ncol cell columns (all of y and z): the tensor's in-plane
+// spectra [6][Pz][Pc2] (one real each), the padded M | H buffer [6][Ptot], the transformed
+// M | H [6][Pc] and the cuFFT plans (3 Pz in-plane transforms per call).
 struct DemagGrid {
     int ncol = 0;
     Pad pd{};
@@ -1058,17 +1160,18 @@ int demag_grid_setup(hamr_ms_t h, DemagGrid &g, int ncol) {
     g.ncol = ncol;
     pd.Px = ncol > 1 ? 2 * ncol : 1;
     pd.Py = P.ncy > 1 ? 2 * P.ncy : 1;
-    pd.Pz = P.ncz > 1 ? 2 * P.ncz : 1;
+    pd.Pz = P.ncz;
     pd.Ptot = (long long)pd.Px * pd.Py * pd.Pz;
-    pd.Pc = (long long)(pd.Px / 2 + 1) * pd.Py * pd.Pz;
+    pd.Pc2 = (long long)(pd.Px / 2 + 1) * pd.Py;
+    pd.Pc = pd.Pc2 * pd.Pz;
+    // plane d of component c: the tensor at z offset d (>= 0), padded in x and y
     std::vector<double> T(6 * (size_t)pd.Ptot, 0.0);
     const unsigned nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
     for (unsigned w = 0; w < nth; ++w)
         pool.emplace_back([&, w]() {
             for (int k = (int)w; k < pd.Pz; k += (int)nth) {
-                const int Z = pad_offset(k, P.ncz, pd.Pz);
-                if (Z == INT32_MIN) continue;
+                const int Z = k;
                 for (int j = 0; j < pd.Py; ++j) {
                     const int Y = pad_offset(j, P.ncy, pd.Py);
                     if (Y == INT32_MIN) continue;
@@ -1085,55 +1188,82 @@ int demag_grid_setup(hamr_ms_t h, DemagGrid &g, int ncol) {
         });
     for (auto &t : pool) t.join();
     std::vector<Real> Tr(T.begin(), T.end());
-    MSCK(h, cudaMalloc(&g.Nh, sizeof(C) * 6 * pd.Pc));
-    MSCK(h, cudaMalloc(&g.Mh, sizeof(C) * 3 * pd.Pc));
+    MSCK(h, cudaMalloc(&g.Nh, sizeof(Real) * 6 * pd.Pc));
+    MSCK(h, cudaMalloc(&g.Mh, sizeof(C) * 6 * pd.Pc));
     // [M | H], each 3 padded grids; the tensor's six components pass through it once at setup
     MSCK(h, cudaMalloc(&g.Mpad, sizeof(Real) * 6 * pd.Ptot));
-    int n[3] = {pd.Pz, pd.Py, pd.Px};
+    int n[2] = {pd.Py, pd.Px};
     const bool dbl = sizeof(Real) == 8;
-    if (cufftPlanMany(&g.plan_f, 3, n, nullptr, 1, (int)pd.Ptot, nullptr, 1, (int)pd.Pc, dbl ? CUFFT_D2Z : CUFFT_R2C,
-                      3) != CUFFT_SUCCESS ||
-        cufftPlanMany(&g.plan_b, 3, n, nullptr, 1, (int)pd.Pc, nullptr, 1, (int)pd.Ptot, dbl ? CUFFT_Z2D : CUFFT_C2R,
-                      3) != CUFFT_SUCCESS)
-        return msfail(h, HAMR_ERR_CUDA, "cuFFT plan creation failed for a %d x %d x %d grid", pd.Px, pd.Py, pd.Pz);
+    const int P2 = pd.Px * pd.Py;
+    if (cufftPlanMany(&g.plan_f, 2, n, nullptr, 1, P2, nullptr, 1, (int)pd.Pc2, dbl ? CUFFT_D2Z : CUFFT_R2C,
+                      3 * pd.Pz) != CUFFT_SUCCESS ||
+        cufftPlanMany(&g.plan_b, 2, n, nullptr, 1, (int)pd.Pc2, nullptr, 1, P2, dbl ? CUFFT_Z2D : CUFFT_C2R,
+                      3 * pd.Pz) != CUFFT_SUCCESS)
+        return msfail(h, HAMR_ERR_CUDA, "cuFFT plan creation failed for %d planes of %d x %d", pd.Pz, pd.Px, pd.Py);
     g.plans = true;
     cufftSetStream(g.plan_f, h->stream);
     cufftSetStream(g.plan_b, h->stream);
     MSCK(h, cudaMemcpyAsync(g.Mpad, Tr.data(), sizeof(Real) * 6 * pd.Ptot, cudaMemcpyHostToDevice, h->stream));
     for (int half = 0; half < 2; ++half) {
         Real *src = (Real *)g.Mpad + (size_t)half * 3 * pd.Ptot;
-        C *dst = (C *)g.Nh + (size_t)half * 3 * pd.Pc;
+        C *dst = (C *)g.Mh + (size_t)half * 3 * pd.Pc;
         const cufftResult r = dbl ? cufftExecD2Z(g.plan_f, (cufftDoubleReal *)src, (cufftDoubleComplex *)dst)
                                   : cufftExecR2C(g.plan_f, (cufftReal *)src, (cufftComplex *)dst);
         if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform of the tensor failed");
     }
+    k_demag_tensor_compress<C, Real><<<nblk(6 * pd.Pc), BLK, 0, h->stream>>>((Real *)g.Nh, (const C *)g.Mh, pd.Pc);
+    MSCK(h, cudaGetLastError());
     MSCK(h, cudaMemsetAsync(g.Mpad, 0, sizeof(Real) * 6 * pd.Ptot, h->stream));
     MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
+}
+
+// The register-blocked z sum for FP32 and a track of 1 to 10 planes (false: not taken).
+template <typename C, typename R>
+bool demag_zmul_r(C *Hh, const C *Mh, const R *Nr, const Pad &pd, cudaStream_t st) {
+    if (!std::is_same<C, cufftComplex>::value) return false;
+    const unsigned nb = (unsigned)((pd.Pc2 + 31) / 32);
+    float2 *H = (float2 *)Hh;
+    const float2 *M = (const float2 *)Mh;
+    const float *N = (const float *)Nr;
+    switch (pd.Pz) {
+#define ZMUL_R(NZ)                                                                    \
+    case NZ:                                                                          \
+        k_demag_zmul_r<NZ><<<nb, dim3(32, NZ < 4 ? NZ : 4), 0, st>>>(H, M, N, pd.Pc2); \
+        return true;
+        ZMUL_R(1) ZMUL_R(2) ZMUL_R(3) ZMUL_R(4) ZMUL_R(5)
+        ZMUL_R(6) ZMUL_R(7) ZMUL_R(8) ZMUL_R(9) ZMUL_R(10)
+#undef ZMUL_R
+        default: return false;
+    }
 }
 
 // The demagnetising field on the target columns [t0, t1) from the sources that `mode` selects
 // (k_demag_M), through grid g placed at column g0, into out (plus `add` where given).
 template <typename Real>
 int demag_pass(hamr_ms_t h, DemagGrid &g, int g0, int mode, int s0, int s1, Real *out, int t0, int t1,
-               const Real *add) {
+               const Real *add, const Real *Mg = nullptr) {
     typedef typename std::conditional<sizeof(Real) == 8, cufftDoubleComplex, cufftComplex>::type C;
     const MsDev &P = h->P;
     const Pad &pd = g.pd;
     const dim3 gc = grid3(g.ncol, P.ncy, P.ncz);
     k_demag_M<Real><<<gc, BLK3, 0, h->stream>>>((Real *)g.Mpad, (const Real *)h->wn, (const Real *)h->m, h->me,
-                                                h->grain_d, P, pd, h->ox, g0, g.ncol, s0, s1, mode);
+                                                h->grain_d, P, pd, h->ox, g0, g.ncol, s0, s1, mode, Mg);
     MSCK(h, cudaGetLastError());
     const bool dbl = sizeof(Real) == 8;
     cufftResult r = dbl ? cufftExecD2Z(g.plan_f, (cufftDoubleReal *)g.Mpad, (cufftDoubleComplex *)g.Mh)
                         : cufftExecR2C(g.plan_f, (cufftReal *)g.Mpad, (cufftComplex *)g.Mh);
     if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT forward transform failed");
-    k_demag_multiply<C><<<nblk(pd.Pc), BLK, 0, h->stream>>>((C *)g.Mh, (const C *)g.Nh, pd.Pc);
+    C *Hh = (C *)g.Mh + 3 * pd.Pc;
+    if (!demag_zmul_r<C, Real>(Hh, (const C *)g.Mh, (const Real *)g.Nh, pd, h->stream)) {
+        const dim3 gz(nblk(pd.Pc2), (unsigned)pd.Pz);
+        k_demag_zmul<C, Real><<<gz, BLK, 0, h->stream>>>(Hh, (const C *)g.Mh, (const Real *)g.Nh, pd.Pc2, pd.Pz);
+    }
     MSCK(h, cudaGetLastError());
     // H goes to the second half of the buffer: the padding of M (first half) must stay zero
     Real *H = (Real *)g.Mpad + 3 * pd.Ptot;
-    r = dbl ? cufftExecZ2D(g.plan_b, (cufftDoubleComplex *)g.Mh, (cufftDoubleReal *)H)
-            : cufftExecC2R(g.plan_b, (cufftComplex *)g.Mh, (cufftReal *)H);
+    r = dbl ? cufftExecZ2D(g.plan_b, (cufftDoubleComplex *)Hh, (cufftDoubleReal *)H)
+            : cufftExecC2R(g.plan_b, (cufftComplex *)Hh, (cufftReal *)H);
     if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT inverse transform failed");
     k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>(out, H, P, pd, g0, g.ncol, t0, t1, add);
     MSCK(h, cudaGetLastError());
@@ -1543,6 +1673,27 @@ int hamr_ms_set_demag(hamr_ms_t h, int32_t on) {
     }
     h->demag = true;
     h->fz_dirty = true;
+    return HAMR_OK;
+}
+
+int hamr_ms_demag_field(hamr_ms_t h, const double *M, double *B_out) {
+    if (!h || !M || !B_out) return h ? msfail(h, HAMR_ERR_ARG, "M and B_out must not be NULL") : HAMR_ERR_ARG;
+    if (!h->gtrack.plans) return msfail(h, HAMR_ERR_STATE, "Eq. 7 is off: call hamr_ms_set_demag(h, 1) first");
+    for (long long q = 0; q < 3 * h->P.nc; ++q)
+        if (!isfinite(M[q])) return msfail(h, HAMR_ERR_ARG, "non-finite magnetisation at cell %lld", q / 3);
+    MsDeviceGuard dg(h->device);
+    // M and B_d pass through the RK4 stage planes, which a step rewrites before it reads them
+    MSCK(h, cudaMemcpyAsync(h->stage, M, sizeof(double) * 3 * h->P.nc, cudaMemcpyHostToDevice, h->stream));
+    int rc = ms_to_planes(h, h->V0, h->P.nc);
+    if (rc) return rc;
+    const int nx = h->P.ncx;
+    rc = h->prec == HAMR_FP64
+             ? demag_pass<double>(h, h->gtrack, 0, 3, 0, nx, (double *)h->V1, 0, nx, nullptr, (const double *)h->V0)
+             : demag_pass<float>(h, h->gtrack, 0, 3, 0, nx, (float *)h->V1, 0, nx, nullptr, (const float *)h->V0);
+    if (rc) return rc;
+    if ((rc = ms_from_planes(h, h->V1, h->P.nc))) return rc;
+    MSCK(h, cudaMemcpyAsync(B_out, h->stage, sizeof(double) * 3 * h->P.nc, cudaMemcpyDeviceToHost, h->stream));
+    MSCK(h, cudaStreamSynchronize(h->stream));
     return HAMR_OK;
 }
 

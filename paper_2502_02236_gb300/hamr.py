@@ -30,7 +30,7 @@ EXPORTS = [
     "hamr_ms_create", "hamr_ms_set_grain_map", "hamr_ms_set_temperature_profile",
     "hamr_ms_set_field_sequence", "hamr_ms_set_cells", "hamr_ms_set_window", "hamr_ms_set_moments",
     "hamr_ms_steps", "hamr_ms_read_cells", "hamr_ms_read_moments", "hamr_ms_get_window", "hamr_ms_read_track",
-    "hamr_ms_set_head_profile", "hamr_ms_set_demag", "hamr_ms_set_region",
+    "hamr_ms_set_head_profile", "hamr_ms_set_demag", "hamr_ms_demag_field", "hamr_ms_set_region",
     "hamr_ms_last_error", "hamr_ms_destroy",
 ]
 NOALLOC_MAX_SITES = 131072
@@ -135,6 +135,7 @@ def lib():
             "hamr_ms_read_track": [vp, d, d, i32, i32, i32, vp, vp],
             "hamr_ms_set_head_profile": [vp, d, d, d, d, d],
             "hamr_ms_set_demag": [vp, i32],
+            "hamr_ms_demag_field": [vp, vp, vp],
             "hamr_ms_set_region": [vp, i32],
         }
         for name, args in sig.items():
@@ -466,8 +467,19 @@ class Multiscale:
         self._ck(lib().hamr_ms_set_region(self._h, int(margin)))
 
     def set_demag(self, on=True):
-        """The demagnetising field of Eq. 7 in both regions (FFT convolution)."""
+        """The demagnetising field of Eq. 7 in both regions (FFT convolution in x and y, direct
+        sum along z)."""
         self._ck(lib().hamr_ms_set_demag(self._h, int(bool(on))))
+
+    def demag_field(self, M):
+        """B_d = -mu0 N * M [T] of Eq. 7 on every cell for the given magnetisation M [A/m]
+        ((n_cells, 3)); needs set_demag(True)."""
+        M = np.ascontiguousarray(np.asarray(M, dtype=np.float64).reshape(-1))
+        if M.size != 3 * self.n_cells:
+            raise ValueError("three components per cell")
+        B = np.zeros((self.n_cells, 3))
+        self._ck(lib().hamr_ms_demag_field(self._h, _p(M), _p(B)))
+        return B
 
     def set_cells(self, m):
         m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(-1))
