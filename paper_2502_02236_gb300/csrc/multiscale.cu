@@ -1,18 +1,23 @@
 // The multiscale write window (Sec. II, Fig. 1): a simple-cubic atomistic window embedded in
 // a micromagnetic finite-difference track, exchange coupled across the interface and moving
-// with the laser spot.  FP64 throughout; one thread per atomistic site or per cell.
+// with the laser spot.  The state (spins, cells, fields) is FP64 or FP32, the handle's
+// precision; m_e(T) and the tensor of Eq. 7 are computed in FP64.
 //
 // Per coupled step n -> n+1 (drivers frozen at t_n):
-//   1. k_ms_average   - Eq. 6: every window cell takes the direction of the sum of its sites;
-//   2. k_ms_fused     - the sLLG Heun step of the window (Eq. 1-3), both stages in one pass;
+//   1. k_ms_average_w - Eq. 6: every window cell takes the direction of the sum of its sites;
+//   2. k_mm_prep      - T and m_e(T), the root of the Langevin equation (Sec. II), per cell
+//                       column, and the cells' coefficients Ms = Ms0 m_e, A = A0 m_e^2,
+//                       K = K0 m_e^3, alpha = lambda (1 - T / 3 T_C);
+//   3. with Eq. 7     - k_demag_M, in-plane transforms (cuFFT), k_demag_zmul[_r] (the sum
+//                       along z), inverse transforms, k_demag_extract: B_d of the state at t_n;
+//   4. k_ms_fused     - the sLLG Heun step of the window (Eq. 1-3), both stages in one pass;
 //                       across the window's x faces a bond sees the direction of the
 //                       micromagnetic cell there;
-//   3. k_mm_prep,     - one classical RK4 step of the micromagnetic LLG (Eq. 1 without the
-//      k_mm_stage x4,   thermal field; Eq. 4 on a 6-point Laplacian, Eq. 5) on the cells
-//      k_mm_final       outside the window, with Ms = Ms0 m_e, A = A0 m_e^2, K = K0 m_e^3,
-//                       alpha = lambda (1 - T / 3 T_C) and m_e(T) the root of the Langevin
-//                       equation (Sec. II); window cells stay at their Eq. 6 directions;
-//   4. window moves   - k_ms_average of the trailing column, k_ms_shift of the sites by one
+//   5. k_mm_stage x4  - one classical RK4 step of the micromagnetic LLG (Eq. 1 without the
+//                       thermal field; Eq. 4 on a 6-point Laplacian, Eq. 5) on the cells of
+//                       the simulated region outside the window, the last stage applying the
+//                       update; window cells stay at their Eq. 6 directions;
+//   6. window moves   - k_ms_average_w of the trailing column, k_ms_shift of the sites by one
 //                       cell column, k_ms_thermalise of the new leading column in the cone
 //                       of half-angle theta_max(m_e) (Sec. II).
 // Device layout: cell and site arrays are component planes [3][n]; cell q = cx + ncx (cy +
@@ -493,13 +498,15 @@ __global__ void k_mm_prep(double *me, double *col, Real *coef, const int *grain,
 // window: K = dm/dt at the stage values Vin, acc += w K and Vout = m + c dt K (the next
 // stage's values).  A window cell, and a frozen cell next to the simulated region, writes its
 // m to Vout, so that every stage buffer holds m there (stage 0 reads m itself); the launch
-// covers [e0, e1), one column beyond the region on each side.  The values of non-magnetic
-// cells are never used (they may be unset).  The threads are short and bound by memory
-// latency, so every value a thread may need is loaded before any test.
+// covers [e0, e1), one column beyond the region on each side.  The last stage (last != 0)
+// instead replaces m of each evolved cell by the renormalised RK4 update m + dt/6 (acc + K):
+// a stage reads no other cell's m, so the update can be made in place.  The values of
+// non-magnetic cells are never used (they may be unset).  The threads are short and bound by
+// memory latency, so every value a thread may need is loaded before any test.
 template <typename Real>
-__global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first, int e0, int ne,
-                           int c0, int c1) {
+__global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, Real *m, const Real *coef, const int *grain,
+                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first, int last, int e0,
+                           int ne, int c0, int c1) {
     int cx, cy, cz;
     if (!coords(ne, P.ncy, cx, cy, cz)) return;
     cx += e0;
@@ -532,6 +539,7 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     }
     if (g < 0) return;
     if ((cx >= ox && cx < ox + P.wx) || cx < c0 || cx >= c1) {  // a window or frozen cell: not evolved here
+        if (last) return;
         Vout[q] = mx;
         Vout[P.nc + q] = my;
         Vout[2 * P.nc + q] = mz;
@@ -554,28 +562,23 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, const Real *m
     by += ba.y;
     bz += ba.z;
     const V3<Real> k = rhs<Real>((Real)P.gamma, alpha, vx, vy, vz, cex * lx + bx, cex * ly + by, cex * lz2 + cK * vz + bz);
-    acc[q] = a0 + w * k.x;
-    acc[P.nc + q] = a1 + w * k.y;
-    acc[2 * P.nc + q] = a2 + w * k.z;
+    const Real s0 = a0 + w * k.x, s1 = a1 + w * k.y, s2 = a2 + w * k.z;
+    if (last) {  // the RK4 update m + dt/6 (K1 + 2 K2 + 2 K3 + K4), renormalised; only this cell reads its m
+        const Real h6 = (Real)P.dt / Real(6);
+        const Real ux = mx + h6 * s0, uy = my + h6 * s1, uz = mz + h6 * s2;
+        const Real nv = sqrt(ux * ux + uy * uy + uz * uz);
+        m[q] = ux / nv;
+        m[P.nc + q] = uy / nv;
+        m[2 * P.nc + q] = uz / nv;
+        return;
+    }
+    acc[q] = s0;
+    acc[P.nc + q] = s1;
+    acc[2 * P.nc + q] = s2;
     const Real dt = (Real)P.dt;
     Vout[q] = mx + c * dt * k.x;
     Vout[P.nc + q] = my + c * dt * k.y;
     Vout[2 * P.nc + q] = mz + c * dt * k.z;
-}
-
-template <typename Real>
-__global__ void k_mm_final(Real *m, const Real *acc, const int *grain, MsDev P, int ox, int c0, int ncol) {
-    int cx, cy, cz;
-    if (!coords(ncol, P.ncy, cx, cy, cz)) return;
-    cx += c0;
-    const int q = cell_at(P, cx, cy, cz);
-    if (grain[q] < 0 || (cx >= ox && cx < ox + P.wx)) return;
-    const Real h6 = (Real)P.dt / Real(6);
-    const Real vx = m[q] + h6 * acc[q], vy = m[P.nc + q] + h6 * acc[P.nc + q], vz = m[2 * P.nc + q] + h6 * acc[2 * P.nc + q];
-    const Real nv = sqrt(vx * vx + vy * vy + vz * vz);
-    m[q] = vx / nv;
-    m[P.nc + q] = vy / nv;
-    m[2 * P.nc + q] = vz / nv;
 }
 
 // Sites move back by one cell column (the last column is thermalised afterwards).
@@ -1411,11 +1414,9 @@ int ms_step(hamr_ms_t h) {
         Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
         k_mm_stage<Real><<<grid3(e1 - e0, P.ncy, P.ncz), BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m,
                                                                         (const Real *)h->coef, h->grain_d, P, h->ox,
-                                                                        F, Bd, cst[s], wst[s], s == 0, e0, e1 - e0,
-                                                                        c0, c1);
+                                                                        F, Bd, cst[s], wst[s], s == 0, s == 3, e0,
+                                                                        e1 - e0, c0, c1);
     }
-    k_mm_final<Real><<<grid3(c1 - c0, P.ncy, P.ncz), BLK3, 0, st>>>(m, (const Real *)h->acc, h->grain_d, P, h->ox, c0,
-                                                                   c1 - c0);
     MSCK(h, cudaGetLastError());
     h->step += 1;
     return HAMR_OK;
