@@ -922,6 +922,10 @@ struct hamr_ms_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // a second stream for the parts of a step that do not depend on one another, and the
+    // events that fork it from the handle's stream and join it back
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     MsDev P{};
     ReplicaDev D{};               // laser spot and write field (the atomistic driver fields)
     std::vector<uint8_t> bits_h;
@@ -993,6 +997,14 @@ struct MsDeviceGuard {
 };
 
 void ms_free(hamr_ms_t h) {
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+        h->side = nullptr;
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->ev_fork = h->ev_join = nullptr;
     void **bufs[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef, &h->S, &h->S2};
     for (void **b : bufs)
         if (*b) {
@@ -1333,7 +1345,8 @@ int ms_thermalise(hamr_ms_t h, int cx0, int cx1, double t, bool all) {
 }
 
 template <typename Real>
-int ms_average(hamr_ms_t h, int cx0, int ncol) {
+int ms_average(hamr_ms_t h, int cx0, int ncol, cudaStream_t st = nullptr) {
+    if (!st) st = h->stream;
     const MsDev &P = h->P;
     const long long n = (long long)ncol * P.ncy * P.ncz;
     Real *m = (Real *)h->m, *wn = (Real *)h->wn;
@@ -1341,14 +1354,14 @@ int ms_average(hamr_ms_t h, int cx0, int ncol) {
 #define MS_AVG(RT)                                                                                       \
     do {                                                                                                 \
         const long long nthr = 32LL * ((ncol + 32 / RT - 1) / (32 / RT)) * P.ncy * P.ncz;                \
-        k_ms_average_w<Real, RT><<<nblk(nthr), BLK, 0, h->stream>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol); \
+        k_ms_average_w<Real, RT><<<nblk(nthr), BLK, 0, st>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol);         \
     } while (0)
     switch (P.r) {
         case 1: MS_AVG(1); break;
         case 2: MS_AVG(2); break;
         case 4: MS_AVG(4); break;
         default:
-            k_ms_average<Real><<<nblk(n), BLK, 0, h->stream>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol);
+            k_ms_average<Real><<<nblk(n), BLK, 0, st>>>(m, wn, S, h->grain_d, P, h->ox, cx0, ncol);
             break;
     }
 #undef MS_AVG
@@ -1367,9 +1380,16 @@ int ms_target(const hamr_ms_t h, double t) {
 template <typename Real>
 int ms_step(hamr_ms_t h) {
     const MsDev &P = h->P;
-    cudaStream_t st = h->stream;
-    int rc = ms_average<Real>(h, h->ox, P.wx);
+    cudaStream_t st = h->stream, sd = h->side;
+    // Eq. 6 of the window cells (window cells only) and the m_e solve (coefficients only) are
+    // independent; the window step reads neither (its x faces see cells outside the window),
+    // but with Eq. 7 it reads B_d, which needs both.  So the side stream takes Eq. 6 and,
+    // without Eq. 7, the m_e solve too, beside the window step; the RK4 stages wait for both.
+    MSCK(h, cudaEventRecord(h->ev_fork, st));
+    MSCK(h, cudaStreamWaitEvent(sd, h->ev_fork, 0));
+    int rc = ms_average<Real>(h, h->ox, P.wx, sd);
     if (rc) return rc;
+    cudaStream_t sp = h->demag ? st : sd;  // the m_e solve's stream
     Real *S = (Real *)h->S, *m = (Real *)h->m;
     const double t = (double)h->step * P.dt;
     const Field<Real> F = field_of<Real>(h, t);
@@ -1379,12 +1399,14 @@ int ms_step(hamr_ms_t h) {
     ms_region(h, c0, c1);
     const int e0 = std::max(0, c0 - 1), e1 = std::min(P.ncx, c1 + 1);
     const double Bm = field_magnitude_host(h, t);
-    k_mm_prep<Real><<<grid3(c1 - c0, P.ncy, 1), BLK3, 0, st>>>(h->me, h->col, (Real *)h->coef, h->grain_d, h->colmask, P,
+    k_mm_prep<Real><<<grid3(c1 - c0, P.ncy, 1), BLK3, 0, sp>>>(h->me, h->col, (Real *)h->coef, h->grain_d, h->colmask, P,
                                                               h->D, t, field_of<double>(h, t), h->Bm_last, c0, c1 - c0);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
+    MSCK(h, cudaEventRecord(h->ev_join, sd));
     const Real *Bd = nullptr;
     if (h->demag) {
+        MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
         if ((rc = ms_demag_step<Real>(h))) return rc;
         Bd = (const Real *)h->Bd;
     }
@@ -1408,6 +1430,7 @@ int ms_step(hamr_ms_t h) {
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
     std::swap(h->S, h->S2);
+    if (!h->demag) MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
     const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
     for (int s = 0; s < 4; ++s) {
         const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
@@ -1518,6 +1541,17 @@ int hamr_ms_create(hamr_ms_t *out, const hamr_ms_desc *d) {
             return msfail(nullptr, HAMR_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
         }
         h->own_stream = true;
+    }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ms_free(h);
+            if (h->own_stream) cudaStreamDestroy(h->stream);
+            delete h;
+            return msfail(nullptr, HAMR_ERR_CUDA, "side stream or events: %s", cudaGetErrorString(e));
+        }
     }
     const size_t el = h->prec == HAMR_FP64 ? sizeof(double) : sizeof(float);
     void **bufs3c[] = {&h->m, &h->V0, &h->V1, &h->acc, &h->coef};
