@@ -1383,8 +1383,10 @@ int ms_step(hamr_ms_t h) {
     cudaStream_t st = h->stream, sd = h->side;
     // Eq. 6 of the window cells (window cells only) and the m_e solve (coefficients only) are
     // independent; the window step reads neither (its x faces see cells outside the window),
-    // but with Eq. 7 it reads B_d, which needs both.  So the side stream takes Eq. 6 and,
-    // without Eq. 7, the m_e solve too, beside the window step; the RK4 stages wait for both.
+    // but with Eq. 7 it reads B_d, which needs both.  RK4 stages 0-2 write only the stage
+    // buffers and the accumulator; the last stage writes m, which the window step reads at its
+    // faces.  So the side stream takes Eq. 6, the m_e solve (without Eq. 7) and stages 0-2
+    // beside the window step, and the last stage waits for both streams.
     MSCK(h, cudaEventRecord(h->ev_fork, st));
     MSCK(h, cudaStreamWaitEvent(sd, h->ev_fork, 0));
     int rc = ms_average<Real>(h, h->ox, P.wx, sd);
@@ -1403,13 +1405,27 @@ int ms_step(hamr_ms_t h) {
                                                               h->D, t, field_of<double>(h, t), h->Bm_last, c0, c1 - c0);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
-    MSCK(h, cudaEventRecord(h->ev_join, sd));
     const Real *Bd = nullptr;
     if (h->demag) {
+        MSCK(h, cudaEventRecord(h->ev_join, sd));
         MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
         if ((rc = ms_demag_step<Real>(h))) return rc;
         Bd = (const Real *)h->Bd;
+        MSCK(h, cudaEventRecord(h->ev_fork, st));
+        MSCK(h, cudaStreamWaitEvent(sd, h->ev_fork, 0));
     }
+    const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
+    auto stage = [&](int s, cudaStream_t ss) {
+        const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
+        Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
+        k_mm_stage<Real><<<grid3(e1 - e0, P.ncy, P.ncz), BLK3, 0, ss>>>(vin, vout, (Real *)h->acc, m,
+                                                                        (const Real *)h->coef, h->grain_d, P, h->ox,
+                                                                        F, Bd, cst[s], wst[s], s == 0, s == 3, e0,
+                                                                        e1 - e0, c0, c1);
+    };
+    for (int s = 0; s < 3; ++s) stage(s, sd);
+    MSCK(h, cudaGetLastError());
+    MSCK(h, cudaEventRecord(h->ev_join, sd));
     // both Heun stages of the window in one pass, into the second buffer
     const dim3 gw((unsigned)((P.nxw + MWX - 1) / MWX), (unsigned)((P.nyw + MWY - 1) / MWY),
                   (unsigned)((P.nzw + MWZ - 1) / MWZ));
@@ -1430,16 +1446,8 @@ int ms_step(hamr_ms_t h) {
 #undef MS_HEUN
     MSCK(h, cudaGetLastError());
     std::swap(h->S, h->S2);
-    if (!h->demag) MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
-    const Real cst[4] = {Real(0.5), Real(0.5), Real(1), Real(0)}, wst[4] = {Real(1), Real(2), Real(2), Real(1)};
-    for (int s = 0; s < 4; ++s) {
-        const Real *vin = s == 0 ? (const Real *)m : (const Real *)((s & 1) ? h->V1 : h->V0);
-        Real *vout = (Real *)((s & 1) ? h->V0 : h->V1);
-        k_mm_stage<Real><<<grid3(e1 - e0, P.ncy, P.ncz), BLK3, 0, st>>>(vin, vout, (Real *)h->acc, m,
-                                                                        (const Real *)h->coef, h->grain_d, P, h->ox,
-                                                                        F, Bd, cst[s], wst[s], s == 0, s == 3, e0,
-                                                                        e1 - e0, c0, c1);
-    }
+    MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+    stage(3, st);
     MSCK(h, cudaGetLastError());
     h->step += 1;
     return HAMR_OK;
