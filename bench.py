@@ -556,6 +556,7 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": args.workload, "replicas": len(w["replicas"]), "lattice_sites": n_sites,
                       "magnetic_sites": n_mag, "record_every": rec, "tile": list(tile),
+                      "plane_range": lat.query(6), "work_items": lat.query(5),
                       "l2": l2_note(n_sites),
                       "parallelism": "replica batches per GPU, no collective"},
            "magnetic_spin_steps_per_s": n_mag * K * dist.world / (ms / 1e3),

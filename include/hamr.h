@@ -211,7 +211,10 @@ int hamr_load_state(hamr_t h, const char *path);
  * (one or two per thread); the split is chosen per replica by a work model.  Compiled
  * (threads, columns per thread, pitch x rows): (512, 1, 36 x 24), (1024, 1, 68 x 24),
  * (256, 1, 36 x 14), (256, 2, 36 x 24).  hamr_autotune times every compiled shape on the
- * current state (advancing nothing: state and step are restored) and keeps the fastest.
+ * current state (advancing nothing: state and step are restored) and keeps the fastest.  With
+ * the plane-range length left to the work model (hamr_set_plane_range 0), a shape that the
+ * model splits along z is timed on whole columns as well; if whole columns win, the range
+ * length is then fixed at the deepest replica's plane count (hamr_query key 6).
  * Errors: ARG (shape not compiled), STATE, CUDA. */
 int hamr_set_tile(hamr_t h, int32_t threads, int32_t staged);
 int hamr_get_tile(hamr_t h, int32_t *threads, int32_t *staged);

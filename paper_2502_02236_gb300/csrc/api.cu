@@ -1437,24 +1437,47 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     const int cur0 = h->cur;
     float best = 1e30f;
     int bestv = h->variant;
+    // with the range length left to the work model (z_range_set 0), a shape the model splits
+    // along z is also timed on whole columns: the model does not know every shape's costs
+    const int zset0 = h->z_range_set;
+    int maxnz = 1;
+    for (const ReplicaDev &R : h->reps_h) maxnz = std::max(maxnz, R.nz);
+    int bestz = zset0;
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     int rc = HAMR_OK;
+    auto trial = [&](int zset, float &ms) -> int {
+        int r = hamr_set_plane_range(h, zset);
+        if (!r) r = steps_impl(h, steps_per_trial, 0, true);  // warm-up, graph capture
+        if (r) return r;
+        cudaError_t e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess && !(r = steps_impl(h, steps_per_trial, 0, false))) {
+            e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (r) return r;
+        return e == cudaSuccess ? HAMR_OK : fail(h, HAMR_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+    };
     FusedVariant v;
     for (int i = 0; fused_variant(i, v); ++i) {
         if (fused_max_blocks_per_sm(i, tetragonal(h)) < 1) continue;
         if ((rc = hamr_set_tile(h, v.threads, v.staged))) break;
-        if ((rc = steps_impl(h, steps_per_trial, 0, true))) break;  // warm-up, graph capture
-        CK(h, cudaEventRecord(e0, h->stream));
-        if ((rc = steps_impl(h, steps_per_trial, 0, false))) break;
-        CK(h, cudaEventRecord(e1, h->stream));
-        CK(h, cudaEventSynchronize(e1));
         float ms = 0;
-        CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        if ((rc = trial(zset0, ms))) break;
         if (ms < best) {
             best = ms;
             bestv = i;
+            bestz = zset0;
+        }
+        if (zset0 == 0 && h->z_split && maxnz > 1) {
+            if ((rc = trial(maxnz, ms))) break;
+            if (ms < best) {
+                best = ms;
+                bestv = i;
+                bestz = maxnz;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -1467,6 +1490,7 @@ int hamr_autotune(hamr_t h, int32_t steps_per_trial) {
     if (rc) return rc;
     if (rc2) return rc2;
     fused_variant(bestv, v);
+    if ((rc = hamr_set_plane_range(h, bestz))) return rc;
     return hamr_set_tile(h, v.threads, v.staged);
 }
 
