@@ -56,6 +56,8 @@ def parse():
                    help="with --workload multiscale_track: the demagnetising field on")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--tile", default=None, help="fused-kernel shape THREADSxSTAGED instead of autotuning")
+    p.add_argument("--planes", type=int, default=0,
+                   help="planes per work item of the fused kernel (0: the library's work model)")
     return p.parse_args()
 
 
@@ -526,6 +528,8 @@ def main():
                 else int(np.prod(rep["dims"])) for rep in w["replicas"])
 
     lat = build_lattice(w, "fp32", dist.rank)
+    if args.planes:
+        lat.set_plane_range(args.planes)
     if args.tile:
         lat.set_tile(*(int(v) for v in args.tile.split("x")))
         tile = lat.get_tile()
