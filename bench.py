@@ -416,8 +416,11 @@ def multiscale_line(args, dist):
             "fp64": {"ms_per_step": t64, "window_spin_steps_per_s": nw * dist.world / (t64 / 1e3), "steps": K},
             "speedup_fp32_over_fp64": t64 / t32,
             "fp32_with_demag": {"ms_per_step": t32d, "window_spin_steps_per_s": nw * dist.world / (t32d / 1e3),
-                                "steps": K, "note": "Eq. 7 by FFT convolution on the 1000 x 120 x 20 padded grid"},
-            "launches_per_step": 10, "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot"}
+                                "steps": K, "note": "Eq. 7: in-plane FFTs on the 1000 x 120 padded grid, direct "
+                                                    "sum over the 10 planes"},
+            "launches_per_step": 7, "streams": 2,
+            "note": "1 nm cells, 0.25 nm sites, 8 nm grains, window follows the spot; Eq. 6, the m_e solve and "
+                    "RK4 stages 0-2 on a second stream beside the window step"}
     # the simulated region (Sec. II, Fig. 1): the window and 60 cell columns on each side evolve,
     # the rest of the track is frozen; the step's cost follows the region, not the track
     reg = {}
