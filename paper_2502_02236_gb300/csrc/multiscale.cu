@@ -300,28 +300,42 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     const int cy = yin ? per_cell<RT>(P, j) : 0;
     const int cxs = site ? ox + per_cell<RT>(P, i) : 0;
     const int lz = P.ncx * P.ncy;
-    // S and grain code of this column at plane k (0 off the window and off the track)
+    // S and grain code of this column at plane k (0 off the window and off the track).  Planes
+    // are loaded in increasing order, so the grain code (and an interface cell's m) is read
+    // once per cell plane (the test on the cell index is the same for the whole CTA).
+    int lcz = -1, lgq = -1;
+    V3<Real> lm = {0, 0, 0};
     auto load = [&](int k, V4<Real> &v) {
         v.x = v.y = v.z = v.g = Real(0);
         if (k < 0 || k >= P.nzw) return;
+        const int cz = per_cell<RT>(P, k);
+        if (cz != lcz) {
+            lcz = cz;
+            lgq = -1;
+            if (site) {
+                lgq = grain[cxs + P.ncx * cy + lz * cz];
+            } else if (icx >= 0) {
+                const int q = icx + P.ncx * cy + lz * cz;
+                lgq = grain[q];
+                if (lgq >= 0) lm = {m[q], m[P.nc + q], m[2 * P.nc + q]};
+            }
+        }
+        if (lgq < 0) return;
         if (site) {
-            const int gq = grain[cxs + P.ncx * cy + lz * per_cell<RT>(P, k)];
-            if (gq < 0) return;
             const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
             v.x = Sin[s];
             v.y = Sin[P.nw + s];
             v.z = Sin[2 * P.nw + s];
-            v.g = (Real)(gq + 1);
-        } else if (icx >= 0) {
-            const int q = icx + P.ncx * cy + lz * per_cell<RT>(P, k);
-            const int gq = grain[q];
-            if (gq < 0) return;
-            v.x = m[q];
-            v.y = m[P.nc + q];
-            v.z = m[2 * P.nc + q];
-            v.g = (Real)(gq + 1);
+        } else {
+            v.x = lm.x;
+            v.y = lm.y;
+            v.z = lm.z;
         }
+        v.g = (Real)(lgq + 1);
     };
+    // B_d of the predicted plane's cell, read once per cell plane
+    int bcz = -1;
+    V3<Real> bd = {0, 0, 0};
     // per-column drivers: the laser's thermal-field scale and the applied field along x
     const Real t = (Real)step * (Real)P.dt, a = (Real)P.a;
     const Real xs = ((Real)ox * P.r + i + Real(0.5)) * a;
@@ -359,10 +373,15 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
             normals3(philox_site(P.key0, P.key1, sidx, (unsigned long long)step), n0, n1, n2);
             V3<Real> ba = ba0;
             if (Bd) {  // the demagnetising field of the site's cell (Eq. 7)
-                const int qs = cxs + P.ncx * cy + lz * per_cell<RT>(P, k);
-                ba.x += Bd[qs];
-                ba.y += Bd[P.nc + qs];
-                ba.z += Bd[2 * P.nc + qs];
+                const int cz = per_cell<RT>(P, k);
+                if (cz != bcz) {
+                    bcz = cz;
+                    const int qs = cxs + P.ncx * cy + lz * cz;
+                    bd = {Bd[qs], Bd[P.nc + qs], Bd[2 * P.nc + qs]};
+                }
+                ba.x += bd.x;
+                ba.y += bd.y;
+                ba.z += bd.z;
             }
             hx = ba.x + sig * n0;
             hy = ba.y + sig * n1;

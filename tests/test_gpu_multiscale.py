@@ -186,6 +186,27 @@ def test_demag_matches_oracle(prec):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("demag,margin", [(False, -1), (True, -1), (False, 4), (True, 4)])
+def test_two_stream_step_is_deterministic(prec, demag, margin):
+    """A step runs Eq. 6, the m_e solve and RK4 stages 0-2 on a second stream beside the
+    window step: two runs of the same sequence (steps, a window move, steps) give bitwise the
+    same cells and spins, so no kernel reads what the other stream has not yet written."""
+    w = I.multiscale_track(ncx=30, ncy=6, ncz=3, cell=1e-9, ratio=4, wx=6, grain_d=5e-9, seed=43, v=2.5e5,
+                           x_spot=8.013e-9)
+    out = []
+    for _ in range(2):
+        p, O, G = pair(w, prec, demag=demag, margin=margin)
+        with G:
+            start(w, p, O, G, orc.ms_target(p, 0.0))
+            G.steps(40, follow=True)
+            G.steps(40, follow=True)
+            out.append((G.read_cells(), G.read_moments(), G.window()))
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("ncz", [1, 3, 10, 11])
 def test_demag_field_matches_direct_sum(prec, ncz):
     """Eq. 7 alone: B_d of a given magnetisation by the GPU's convolution (in-plane FFTs on the
