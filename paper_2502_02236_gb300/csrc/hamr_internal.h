@@ -61,7 +61,7 @@ struct Ctl {
     unsigned work_ctr[2];    // work-list counters of the persistent kernel (by step parity)
     int err;                 // error flags (bit 0: bad value found by the finite check;
                              // bit 1: a bounded wait of the fused kernel ran out)
-    int pad_;
+    int ticket;              // blocks of a record's bookkeeping that are done (0 between launches)
 };
 
 // One unit of work of the fused kernel: a block of columns of one replica.

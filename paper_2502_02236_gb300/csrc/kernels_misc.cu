@@ -7,58 +7,73 @@ namespace hamr {
 
 // After a block of G steps: advance the step counter and, at a record point, turn the
 // per-grain FP64 sums into the replica magnetisation M = sum S / N_mag (Eq. 6 as an
-// average over magnetic sites), per-grain averages, and clear the sums.
-__global__ void k_bookkeeping(Ctl *ctl, int G, int record, int R, const ReplicaDev *reps, const long long *nmag,
-                              const long long *gcount, int Gtot, double *grain_acc, unsigned long long *grain_fx,
-                              double *grain_last, double *rec, long long rec_cap, long long *rec_step) {
+// average over magnetic sites), per-grain averages, and clear the sums.  A record launch has
+// one block per replica: the block folds the FP32 path's exact fixed-point sums (units of
+// 2^-24) of its grains into their FP64 sums, writes the grain averages, clears both and
+// reduces its replica's M over a fixed tree.  Every block reads the step counter and the
+// record index before any is changed: the last block to finish (a ticket counted in ctl)
+// advances them.
+constexpr int BK_THREADS = 128;
+__global__ void __launch_bounds__(BK_THREADS) k_bookkeeping(Ctl *ctl, int G, int record, const ReplicaDev *reps,
+                                                             const long long *nmag, const long long *gcount,
+                                                             double *grain_acc, unsigned long long *grain_fx,
+                                                             double *grain_last, double *rec, long long rec_cap,
+                                                             long long *rec_step, int R) {
     const long long after = ctl->step + G;
-    if (record) {
-        // fold the FP32 path's exact fixed-point sums (units of 2^-24) into the FP64 sums
-        for (int g = threadIdx.x; g < 3 * Gtot; g += blockDim.x) {
-            grain_acc[g] += (double)(long long)grain_fx[g] * 5.9604644775390625e-08;
-            grain_fx[g] = 0ull;
+    if (!record) {
+        if (threadIdx.x == 0) ctl->step = after;
+        return;
+    }
+    const long long idx = ctl->n_rec;
+    const int r = blockIdx.x;
+    const int g0 = reps[r].grain_off, ng = reps[r].n_grains;
+    double mx = 0, my = 0, mz = 0;
+    for (int g = g0 + (int)threadIdx.x; g < g0 + ng; g += BK_THREADS) {
+        double t[3];
+        for (int d = 0; d < 3; ++d) {
+            t[d] = grain_acc[3 * g + d] + (double)(long long)grain_fx[3 * g + d] * 5.9604644775390625e-08;
+            grain_acc[3 * g + d] = 0.0;
+            grain_fx[3 * g + d] = 0ull;
         }
+        mx += t[0];
+        my += t[1];
+        mz += t[2];
+        const double c = (double)gcount[g];
+        for (int d = 0; d < 3; ++d) grain_last[3 * g + d] = c > 0 ? t[d] / c : 0.0;
+    }
+    __shared__ double sm[3][BK_THREADS];
+    sm[0][threadIdx.x] = mx;
+    sm[1][threadIdx.x] = my;
+    sm[2][threadIdx.x] = mz;
+    __syncthreads();
+    for (int w = BK_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int d = 0; d < 3; ++d) sm[d][threadIdx.x] += sm[d][threadIdx.x + w];
         __syncthreads();
-        const long long idx = ctl->n_rec;
-        for (int r = threadIdx.x; r < R; r += blockDim.x) {
-            const int g0 = reps[r].grain_off, ng = reps[r].n_grains;
-            double mx = 0, my = 0, mz = 0;
-            for (int g = g0; g < g0 + ng; ++g) {
-                mx += grain_acc[3 * g];
-                my += grain_acc[3 * g + 1];
-                mz += grain_acc[3 * g + 2];
-            }
-            const double nm = (double)nmag[r];
-            if (idx < rec_cap) {
-                double *o = rec + (idx * R + r) * 3;
-                o[0] = nm > 0 ? mx / nm : 0.0;
-                o[1] = nm > 0 ? my / nm : 0.0;
-                o[2] = nm > 0 ? mz / nm : 0.0;
-            }
+    }
+    if (threadIdx.x == 0) {
+        const double nm = (double)nmag[r];
+        if (idx < rec_cap) {
+            double *o = rec + (idx * R + r) * 3;
+            for (int d = 0; d < 3; ++d) o[d] = nm > 0 ? sm[d][0] / nm : 0.0;
         }
-        __syncthreads();
-        for (int g = threadIdx.x; g < Gtot; g += blockDim.x) {
-            const double c = (double)gcount[g];
-            for (int d = 0; d < 3; ++d) {
-                grain_last[3 * g + d] = c > 0 ? grain_acc[3 * g + d] / c : 0.0;
-                grain_acc[3 * g + d] = 0.0;
-            }
-        }
-        if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->ticket, 1) == (int)gridDim.x - 1) {  // every block has read ctl
             if (idx < rec_cap) rec_step[idx] = after;
             ctl->n_rec = idx + 1;
+            ctl->step = after;
+            ctl->ticket = 0;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) ctl->step = after;
 }
 
 cudaError_t launch_bookkeeping(Ctl *ctl, int G, bool record, int R, const ReplicaDev *reps, const long long *nmag,
                                const long long *gcount, int Gtot, double *grain_acc, unsigned long long *grain_fx,
                                double *grain_last, double *rec, long long rec_cap, long long *rec_step,
                                cudaStream_t st) {
-    k_bookkeeping<<<1, 256, 0, st>>>(ctl, G, record ? 1 : 0, R, reps, nmag, gcount, Gtot, grain_acc, grain_fx,
-                                     grain_last, rec, rec_cap, rec_step);
+    (void)Gtot;
+    k_bookkeeping<<<record ? R : 1, BK_THREADS, 0, st>>>(ctl, G, record ? 1 : 0, reps, nmag, gcount, grain_acc,
+                                                         grain_fx, grain_last, rec, rec_cap, rec_step, R);
     return cudaGetLastError();
 }
 
