@@ -338,7 +338,10 @@ typedef struct {
     int32_t precision;       /* HAMR_FP64: everything in FP64.  HAMR_FP32: spins, cells and
                                 field arithmetic in FP32 (m_e(T) is solved in FP64) */
     int32_t device;
-    void *stream;            /* cudaStream_t, or NULL for a library-owned stream */
+    void *stream;            /* cudaStream_t, or NULL for a library-owned stream.  Work is
+                                ordered on this stream; within a step the handle also runs
+                                the parts that do not depend on one another on a second,
+                                library-owned stream, forked from and joined back to it */
 } hamr_ms_desc;
 
 /* Allocates the track and the window (errors: ARG, OOM, CUDA; message in
