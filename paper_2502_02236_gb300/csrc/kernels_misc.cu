@@ -96,15 +96,29 @@ __global__ void __launch_bounds__(PLAIN_BLOCK) k_grain_sums_fx(
     const unsigned long long mine = lane < it.n_runs ? runs[it.run0 + lane] : 0ull;
     const float *__restrict__ S = ((ctl->step + G) & 1) ? S1 : S0;
     int sx = 0, sy = 0, sz = 0;
-#pragma unroll 4
-    for (int k = 0; k < it.n_runs; ++k) {
-        const unsigned long long rw = __shfl_sync(full, mine, k);
-        const long long j = (long long)(rw >> 5) + lane;
-        if (lane <= (int)(rw & 31ull)) {
-            sx += __float2int_rn(S[j] * FX_SCALE);
-            sy += __float2int_rn(S[NS + j] * FX_SCALE);
-            sz += __float2int_rn(S[2 * NS + j] * FX_SCALE);
+    // eight runs at a time, every load issued before any is used: a lane past its run's end
+    // (or past the item's last run) reads the run's first slot, a valid address, and drops it
+    constexpr int RB = 8;
+    for (int k0 = 0; k0 < it.n_runs; k0 += RB) {
+        float vx[RB], vy[RB], vz[RB];
+        bool on[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int k = k0 + u;
+            const unsigned long long rw = __shfl_sync(full, mine, k & 31);
+            on[u] = k < it.n_runs && lane <= (int)(rw & 31ull);
+            const long long j = (long long)(rw >> 5) + (on[u] ? lane : 0);
+            vx[u] = S[j];
+            vy[u] = S[NS + j];
+            vz[u] = S[2 * NS + j];
         }
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+            if (on[u]) {
+                sx += __float2int_rn(vx[u] * FX_SCALE);
+                sy += __float2int_rn(vy[u] * FX_SCALE);
+                sz += __float2int_rn(vz[u] * FX_SCALE);
+            }
     }
     long long tx = sx, ty = sy, tz = sz;
 #pragma unroll
