@@ -305,7 +305,16 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     // once per cell plane (the test on the cell index is the same for the whole CTA).
     int lcz = -1, lgq = -1;
     V3<Real> lm = {0, 0, 0};
+    // site indices advance by one plane per call (planes are loaded in order, from z0 - 2; the
+    // unsigned arithmetic wraps back to the right value once k >= 0); the component planes are
+    // addressed from 64-bit bases
+    const unsigned pw = (unsigned)P.nxw * (unsigned)P.nyw;
+    const unsigned scol = site ? (unsigned)i + (unsigned)P.nxw * (unsigned)j : 0u;
+    const Real *Sx = Sin, *Sy = Sin + P.nw, *Sz = Sin + 2 * P.nw;
+    unsigned sld = scol + pw * (unsigned)(z0 - 2);
     auto load = [&](int k, V4<Real> &v) {
+        const unsigned sk_ = sld;
+        sld += pw;
         v.x = v.y = v.z = v.g = Real(0);
         if (k < 0 || k >= P.nzw) return;
         const int cz = per_cell<RT>(P, k);
@@ -322,10 +331,9 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
         }
         if (lgq < 0) return;
         if (site) {
-            const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * k);
-            v.x = Sin[s];
-            v.y = Sin[P.nw + s];
-            v.z = Sin[2 * P.nw + s];
+            v.x = Sx[sk_];
+            v.y = Sy[sk_];
+            v.z = Sz[sk_];
         } else {
             v.x = lm.x;
             v.y = lm.y;
@@ -359,16 +367,22 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     // the corrector base S + dt/2 f1 and the S-independent field (applied, thermal) of the
     // plane awaiting correction; the own S' of planes k - 2 and k - 1
     Real amx = 0, amy = 0, amz = 0, hmx = 0, hmy = 0, hmz = 0;
+    // running indices of plane k (from z0 - 1): S slot k mod 3, S' slot k mod 4, the site of
+    // the plane being corrected (k - 1) and plane k's Philox counter
+    int sk = (z0 + 2) % 3, pk = (z0 + 3) & 3;
+    unsigned sst = scol + pw * (unsigned)(z0 - 2);
+    Real *Ox = Sout, *Oy = Sout + P.nw, *Oz = Sout + 2 * P.nw;
+    unsigned long long sidx = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * (unsigned long long)(z0 - 1));
+    const unsigned long long dsid = NX * (unsigned long long)P.nyw;
     for (int k = z0 - 1; k <= z1; ++k) {
         load(k + 2, p2);  // consumed two steps on: its latency overlaps this step
-        const int sk = (k + 3) % 3, pk = (k + 4) & 3;
+        const int sk1 = sk == 2 ? 0 : sk + 1;
         // ---- predictor on plane k
         V4<Real> sp = {0, 0, 0, 0};
         Real anx = 0, any = 0, anz = 0, hx = 0, hy = 0, hz = 0;
         if (icx >= 0) {
             sp = c0;  // an interface cell: S' = m (frozen for the step)
         } else if (site && pred && k >= 0 && k < P.nzw && c0.g != Real(0)) {
-            const unsigned long long sidx = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * k);
             Real n0, n1, n2;
             normals3(philox_site(P.key0, P.key1, sidx, (unsigned long long)step), n0, n1, n2);
             V3<Real> ba = ba0;
@@ -413,15 +427,14 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
         }
         if (own) {
             sP[pk][tid] = sp;
-            sS[(k + 4) % 3][tid] = p1;  // S of plane k + 1, read by the next step's predictor
+            sS[sk1][tid] = p1;  // S of plane k + 1, read by the next step's predictor
         }
         __syncthreads();
         // ---- corrector on plane k - 1 (the tile's columns)
         const int kc = k - 1;
         if (inner && kc >= z0 && kc < z1) {
-            const V4<Real> *Q = sP[(kc + 4) & 3];
+            const V4<Real> *Q = sP[(pk + 3) & 3];
             const V4<Real> v = Q[tid];
-            const long long s = i + (long long)P.nxw * (j + (long long)P.nyw * kc);
             Real ox_ = 0, oy_ = 0, oz_ = 0;
             if (v.g != Real(0)) {
                 const Real g = v.g;
@@ -437,7 +450,7 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
                 add(Q[tid + 1]);
                 add(Q[tid - MWSX]);
                 add(Q[tid + MWSX]);
-                add(sP[(kc + 3) & 3][tid]);  // S'(k - 2), own
+                add(sP[(pk + 2) & 3][tid]);  // S'(k - 2), own
                 add(sp);                     // S'(k), own
                 const V3<Real> f = rhs<Real>((Real)P.gamma, (Real)P.lambda, v.x, v.y, v.z, Jm * ex + hmx,
                                              Jm * ey + hmy, Jm * ez + Km * v.z + hmz);
@@ -447,10 +460,14 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
                 oy_ = wy * in;
                 oz_ = wz * in;
             }
-            Sout[s] = ox_;
-            Sout[P.nw + s] = oy_;
-            Sout[2 * P.nw + s] = oz_;
+            Ox[sst] = ox_;
+            Oy[sst] = oy_;
+            Oz[sst] = oz_;
         }
+        sk = sk1;
+        pk = (pk + 1) & 3;
+        sst += pw;
+        sidx += dsid;
         m1 = c0;
         c0 = p1;
         p1 = p2;
