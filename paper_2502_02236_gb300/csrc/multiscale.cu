@@ -302,7 +302,9 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     const int lz = P.ncx * P.ncy;
     // S and grain code of this column at plane k (0 off the window and off the track).  Planes
     // are loaded in increasing order, so the grain code (and an interface cell's m) is read
-    // once per cell plane (the test on the cell index is the same for the whole CTA).
+    // once per cell plane (the test on the cell index is the same for the whole CTA).  load()
+    // only issues the reads; finish() applies the grain code when the plane is first used, a
+    // march step later, so no thread waits on a read it has just issued.
     int lcz = -1, lgq = -1;
     V3<Real> lm = {0, 0, 0};
     // site indices advance by one plane per call (planes are loaded in order, from z0 - 2; the
@@ -312,29 +314,38 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     const unsigned scol = site ? (unsigned)i + (unsigned)P.nxw * (unsigned)j : 0u;
     const Real *Sx = Sin, *Sy = Sin + P.nw, *Sz = Sin + 2 * P.nw;
     unsigned sld = scol + pw * (unsigned)(z0 - 2);
-    auto load = [&](int k, V4<Real> &v) {
+    auto load = [&](int k, V4<Real> &v, bool &in) {
         const unsigned sk_ = sld;
         sld += pw;
+        in = k >= 0 && k < P.nzw;
         v.x = v.y = v.z = v.g = Real(0);
-        if (k < 0 || k >= P.nzw) return;
-        const int cz = per_cell<RT>(P, k);
-        if (cz != lcz) {
-            lcz = cz;
-            lgq = -1;
-            if (site) {
-                lgq = grain[cxs + P.ncx * cy + lz * cz];
-            } else if (icx >= 0) {
-                const int q = icx + P.ncx * cy + lz * cz;
-                lgq = grain[q];
-                if (lgq >= 0) lm = {m[q], m[P.nc + q], m[2 * P.nc + q]};
+        if (in) {
+            const int cz = per_cell<RT>(P, k);
+            if (cz != lcz) {
+                lcz = cz;
+                if (site) {
+                    lgq = grain[cxs + P.ncx * cy + lz * cz];
+                } else if (icx >= 0) {
+                    const int q = icx + P.ncx * cy + lz * cz;
+                    lgq = grain[q];
+                    lm = {m[q], m[P.nc + q], m[2 * P.nc + q]};
+                }
             }
         }
-        if (lgq < 0) return;
-        if (site) {
-            v.x = Sx[sk_];
-            v.y = Sy[sk_];
-            v.z = Sz[sk_];
-        } else {
+        if (site) {  // a valid slot off the window's planes, its value dropped by finish()
+            const unsigned ix = in ? sk_ : scol;
+            v.x = Sx[ix];
+            v.y = Sy[ix];
+            v.z = Sz[ix];
+        }
+    };
+    // the plane last loaded, with its cell's grain code (and, for an interface column, m)
+    auto finish = [&](V4<Real> &v, bool in) {
+        if (!in || lgq < 0) {
+            v.x = v.y = v.z = v.g = Real(0);
+            return;
+        }
+        if (!site) {
             v.x = lm.x;
             v.y = lm.y;
             v.z = lm.z;
@@ -359,9 +370,12 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
 
     // prologue: S of planes z0 - 2 .. z0 in registers, plane z0 - 1 staged
     V4<Real> m1, c0, p1, p2;
-    load(z0 - 2, m1);
-    load(z0 - 1, c0);
-    load(z0, p1);
+    bool in1, in2;
+    load(z0 - 2, m1, in1);
+    finish(m1, in1);
+    load(z0 - 1, c0, in1);
+    finish(c0, in1);
+    load(z0, p1, in1);
     if (own) sS[(z0 + 2) % 3][tid] = c0;
     __syncthreads();
     // the corrector base S + dt/2 f1 and the S-independent field (applied, thermal) of the
@@ -375,7 +389,8 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     unsigned long long sidx = X + NX * ((unsigned long long)j + (unsigned long long)P.nyw * (unsigned long long)(z0 - 1));
     const unsigned long long dsid = NX * (unsigned long long)P.nyw;
     for (int k = z0 - 1; k <= z1; ++k) {
-        load(k + 2, p2);  // consumed two steps on: its latency overlaps this step
+        finish(p1, in1);      // plane k + 1, loaded a step ago
+        load(k + 2, p2, in2);  // finished next step: its latency overlaps this step
         const int sk1 = sk == 2 ? 0 : sk + 1;
         // ---- predictor on plane k
         V4<Real> sp = {0, 0, 0, 0};
@@ -471,6 +486,7 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
         m1 = c0;
         c0 = p1;
         p1 = p2;
+        in1 = in2;
         amx = anx;
         amy = any;
         amz = anz;
