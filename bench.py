@@ -459,7 +459,54 @@ def multiscale_line(args, dist):
                    "what": "3 coupled steps of the full track from the same state, every cell and window spin"}
             G.close()
             (line[key] if key else line)["oracle_err"] = err
+        line["region"]["oracle_err"] = ms_oracle_err(w, "fp32", margin=60)
+        line["region"]["oracle_err"]["what"] = "3 coupled steps of the full track, 60 columns each side evolved"
+        # Eq. 7: the oracle sums over every pair of cells, so its error is taken on a shorter,
+        # thinner track that runs the same kernels (the in-plane transforms and the sum along z)
+        ws = I.multiscale_track(ncx=40, ncy=8, ncz=4, ratio=4, wx=10, grain_d=5e-9, seed=33, x_spot=20.2e-9)
+        for margin, tgt in ((-1, line["fp32_with_demag"]), (8, line["region"])):
+            e = ms_oracle_err(ws, "fp32", margin=margin, demag=True)
+            e["what"] = ("3 coupled steps of a 40 x 8 x 4-cell track (0.25 nm sites, a 10-cell window%s) with "
+                         "Eq. 7" % (", 8 columns each side evolved" if margin >= 0 else ""))
+            tgt["oracle_err_demag" if margin >= 0 else "oracle_err"] = e
     return line
+
+
+def ms_oracle_err(w, precision, margin=-1, demag=False, steps=3):
+    """Largest difference of every cell and window spin to the FP64 oracle after `steps`
+    coupled steps of the multiscale track w from +z cells, the window following the spot."""
+    import oracle as orc
+    from paper_2502_02236_gb300.hamr import Multiscale
+    T, F = w["T"], w["field"]
+    p = orc.MsParams(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                     ku=w["ku"], lam=w["lam"], T_C=w["T_C"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], dt=w["dt"],
+                     seed=w["seed"], **T, B0=F["B0"], direction=F["direction"], bits=F["bits"],
+                     bit_len=F["bit_len"], ramp_len=F["ramp_len"], head_x0=F["head_x0"], head_v=F["head_v"],
+                     demag=demag, margin=margin)
+    m = np.zeros((w["ncx"] * w["ncy"] * w["ncz"], 3))
+    m[:, 2] = 1.0
+    ox = orc.ms_target(p, 0.0)
+    O = orc.MsOracle(p, w["grain"])
+    O.set_cells(m)
+    O.set_window(ox)
+    O.run(steps, follow=True)
+    G = Multiscale(w["ncx"], w["ncy"], w["ncz"], w["cell"], w["ratio"], w["wx"], J=w["J"], mu_s=w["mu_s"],
+                   ku=w["ku"], Ms0=w["Ms0"], A0=w["A0"], K0=w["K0"], lam=w["lam"], T_C=w["T_C"], dt=w["dt"],
+                   seed=w["seed"], precision=precision)
+    G.set_grain_map(w["grain"])
+    G.set_temperature_profile(**T)
+    G.set_field_sequence(**F)
+    G.set_cells(m)
+    if margin >= 0:
+        G.set_region(margin)
+    if demag:
+        G.set_demag(True)
+    G.set_window(ox)
+    G.steps(steps, follow=True)
+    err = {"max_abs_cell": float(np.abs(G.read_cells() - O.cells()).max()),
+           "max_abs_spin": float(np.abs(G.read_moments() - O.moments()).max())}
+    G.close()
+    return err
 
 
 def multiscale_only(args, dist):
