@@ -250,6 +250,31 @@ __global__ void k_ms_average_w(Real *m, Real *wn, const Real *S, const int *grai
 __device__ __forceinline__ float inv_norm(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
 
+// B_d of Eq. 7 read where it is used: s H + add on the cells of a convolution grid whose
+// first column is g0, H the grid's unnormalised inverse transform [3][Ptot] (s = -mu0 / (Px Py))
+// and add the frozen cells' part [3][nc] (or null).  H null: no demagnetising field.  A cell
+// beyond the grid's columns reads its nearest grid column (only cells that are not evolved,
+// whose loads are issued before their tests, ask for one).
+template <typename Real>
+struct BdView {
+    const Real *H = nullptr, *add = nullptr;
+    long long Ptot = 0;
+    int Px = 0, Py = 0, g0 = 0, ncol = 0;
+    Real s = 0;
+    __device__ __forceinline__ V3<Real> at(const MsDev &P, int cx, int cy, int cz, int q) const {
+        int i = cx - g0;
+        i = i < 0 ? 0 : (i >= ncol ? ncol - 1 : i);
+        const long long pp = i + (long long)Px * (cy + (long long)Py * cz);
+        V3<Real> b = {s * H[pp], s * H[Ptot + pp], s * H[2 * Ptot + pp]};
+        if (add) {
+            b.x += add[q];
+            b.y += add[P.nc + q];
+            b.z += add[2 * P.nc + q];
+        }
+        return b;
+    }
+};
+
 // ---------------------------------------------------------------- fused window step
 // Both Heun stages of the window in one pass over its sites (Sec. II, Eq. 1-3): the predictor
 // S' = normalise(S + dt f(S)), the corrector normalise(S + dt/2 f(S) + dt/2 f(S')), both
@@ -279,8 +304,8 @@ struct V4 {
 template <typename Real, int RT>
 __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
     k_ms_fused(const Real *__restrict__ Sin, Real *__restrict__ Sout, const Real *__restrict__ m,
-               const int *__restrict__ grain, MsDev P, ReplicaDev D, Field<Real> F, const Real *__restrict__ Bd,
-               int ox, long long step) {
+               const int *__restrict__ grain, MsDev P, ReplicaDev D, Field<Real> F, BdView<Real> V, int ox,
+               long long step) {
     extern __shared__ unsigned char ms_smem[];
     V4<Real>(*sS)[MWPOS] = reinterpret_cast<V4<Real>(*)[MWPOS]>(ms_smem);  // [3]: S, plane k in slot k mod 3
     V4<Real>(*sP)[MWPOS] = sS + 3;                                          // [4]: S', plane k in slot k mod 4
@@ -401,12 +426,11 @@ __global__ void __launch_bounds__(MWT, sizeof(Real) == 4 ? 2 : 1)
             Real n0, n1, n2;
             normals3(philox_site(P.key0, P.key1, sidx, (unsigned long long)step), n0, n1, n2);
             V3<Real> ba = ba0;
-            if (Bd) {  // the demagnetising field of the site's cell (Eq. 7)
+            if (V.H) {  // the demagnetising field of the site's cell (Eq. 7)
                 const int cz = per_cell<RT>(P, k);
                 if (cz != bcz) {
                     bcz = cz;
-                    const int qs = cxs + P.ncx * cy + lz * cz;
-                    bd = {Bd[qs], Bd[P.nc + qs], Bd[2 * P.nc + qs]};
+                    bd = V.at(P, cxs, cy, cz, cxs + P.ncx * cy + lz * cz);
                 }
                 ba.x += bd.x;
                 ba.y += bd.y;
@@ -557,7 +581,7 @@ __global__ void k_mm_prep(double *me, double *col, Real *coef, const int *grain,
 // memory latency, so every value a thread may need is loaded before any test.
 template <typename Real>
 __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, Real *m, const Real *coef, const int *grain,
-                           MsDev P, int ox, Field<Real> F, const Real *Bd, Real c, Real w, int first, int last, int e0,
+                           MsDev P, int ox, Field<Real> F, BdView<Real> V, Real c, Real w, int first, int last, int e0,
                            int ne, int c0, int c1) {
     int cx, cy, cz;
     if (!coords(ne, P.ncy, cx, cy, cz)) return;
@@ -584,10 +608,11 @@ __global__ void k_mm_stage(const Real *Vin, Real *Vout, Real *acc, Real *m, cons
     const Real a0 = first ? Real(0) : acc[q], a1 = first ? Real(0) : acc[P.nc + q],
                a2 = first ? Real(0) : acc[2 * P.nc + q];
     Real bx = 0, by = 0, bz = 0;
-    if (Bd) {
-        bx = Bd[q];
-        by = Bd[P.nc + q];
-        bz = Bd[2 * P.nc + q];
+    if (V.H) {
+        const V3<Real> b = V.at(P, cx, cy, cz, q);
+        bx = b.x;
+        by = b.y;
+        bz = b.z;
     }
     if (g < 0) return;
     if ((cx >= ox && cx < ox + P.wx) || cx < c0 || cx >= c1) {  // a window or frozen cell: not evolved here
@@ -1002,11 +1027,12 @@ struct hamr_ms_ctx {
     bool grains_set = false, cells_set = false;
     bool window_live = false;     // the window's sites are newer than its cells (placed, cells not replaced since)
     // demagnetising field (Eq. 7): the track's padded grid and, with a simulated region, the
-    // region's; B_d [3][nc]; the frozen cells' part of B_d on the region's cells [3][nc], valid
-    // for the region [fz_c0, fz_c1) until the frozen cells change
+    // region's (B_d is read from the grid's inverse transform where it is used); the frozen
+    // cells' part of B_d on the region's cells [3][nc], valid for the region [fz_c0, fz_c1)
+    // until the frozen cells change
     bool demag = false;
     DemagGrid gtrack, gregion;
-    void *Bd = nullptr, *Bfz = nullptr;
+    void *Bfz = nullptr;
     int fz_c0 = -1, fz_c1 = -1;
     bool fz_dirty = true;
 };
@@ -1063,7 +1089,7 @@ void ms_free(hamr_ms_t h) {
             cudaFree(*b);
             *b = nullptr;
         }
-    void **dbufs[] = {&h->Bd, &h->Bfz};
+    void **dbufs[] = {&h->Bfz};
     for (void **b : dbufs)
         if (*b) {
             cudaFree(*b);
@@ -1306,7 +1332,8 @@ bool demag_zmul_r(C *Hh, const C *Mh, const R *Nr, const Pad &pd, cudaStream_t s
 }
 
 // The demagnetising field on the target columns [t0, t1) from the sources that `mode` selects
-// (k_demag_M), through grid g placed at column g0, into out (plus `add` where given).
+// (k_demag_M), through grid g placed at column g0, into out (plus `add` where given; out null:
+// left in the grid's inverse transform, for a BdView).
 template <typename Real>
 int demag_pass(hamr_ms_t h, DemagGrid &g, int g0, int mode, int s0, int s1, Real *out, int t0, int t1,
                const Real *add, const Real *Mg = nullptr) {
@@ -1332,7 +1359,7 @@ int demag_pass(hamr_ms_t h, DemagGrid &g, int g0, int mode, int s0, int s1, Real
     r = dbl ? cufftExecZ2D(g.plan_b, (cufftDoubleComplex *)Hh, (cufftDoubleReal *)H)
             : cufftExecC2R(g.plan_b, (cufftComplex *)Hh, (cufftReal *)H);
     if (r != CUFFT_SUCCESS) return msfail(h, HAMR_ERR_CUDA, "cuFFT inverse transform failed");
-    k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>(out, H, P, pd, g0, g.ncol, t0, t1, add);
+    if (out) k_demag_extract<Real><<<gc, BLK3, 0, h->stream>>>(out, H, P, pd, g0, g.ncol, t0, t1, add);
     MSCK(h, cudaGetLastError());
     return HAMR_OK;
 }
@@ -1354,12 +1381,29 @@ void ms_region(const hamr_ms_t h, int &c0, int &c1) {
 // padded grid, every step; the frozen cells' part is a convolution over the track's grid with
 // the region left out, kept until the region moves or the frozen cells change.
 template <typename Real>
-int ms_demag_step(hamr_ms_t h) {
+BdView<Real> bd_view(const DemagGrid &g, int g0, const Real *add) {
+    BdView<Real> V;
+    V.H = (const Real *)g.Mpad + 3 * g.pd.Ptot;
+    V.add = add;
+    V.Ptot = g.pd.Ptot;
+    V.Px = g.pd.Px;
+    V.Py = g.pd.Py;
+    V.g0 = g0;
+    V.ncol = g.ncol;
+    V.s = (Real)(-1.25663706212e-6 / ((double)g.pd.Px * g.pd.Py));
+    return V;
+}
+
+template <typename Real>
+int ms_demag_step(hamr_ms_t h, BdView<Real> &V) {
     const MsDev &P = h->P;
     int c0, c1;
     ms_region(h, c0, c1);
     const int L = h->margin < 0 ? P.ncx : std::min(P.ncx, P.wx + 2 * h->margin);
-    if (L >= P.ncx) return demag_pass<Real>(h, h->gtrack, 0, 0, 0, P.ncx, (Real *)h->Bd, 0, P.ncx, nullptr);
+    if (L >= P.ncx) {
+        V = bd_view<Real>(h->gtrack, 0, nullptr);
+        return demag_pass<Real>(h, h->gtrack, 0, 0, 0, P.ncx, (Real *)nullptr, 0, P.ncx, nullptr);
+    }
     if (h->gregion.ncol != L) {
         demag_grid_free(h->gregion);
         int rc = demag_grid_setup<Real>(h, h->gregion, L);
@@ -1372,7 +1416,8 @@ int ms_demag_step(hamr_ms_t h) {
         h->fz_c1 = c1;
         h->fz_dirty = false;
     }
-    return demag_pass<Real>(h, h->gregion, c0, 1, c0, c1, (Real *)h->Bd, c0, c1, (const Real *)h->Bfz);
+    V = bd_view<Real>(h->gregion, c0, (const Real *)h->Bfz);
+    return demag_pass<Real>(h, h->gregion, c0, 1, c0, c1, (Real *)nullptr, c0, c1, nullptr);
 }
 
 // Thermalise the window sites of cell columns [cx0, cx1) at time t.  m_e(T) is solved first
@@ -1457,12 +1502,11 @@ int ms_step(hamr_ms_t h) {
                                                               h->D, t, field_of<double>(h, t), h->Bm_last, c0, c1 - c0);
     h->Bm_last = Bm;
     MSCK(h, cudaGetLastError());
-    const Real *Bd = nullptr;
+    BdView<Real> Bd;  // H null: no demagnetising field
     if (h->demag) {
         MSCK(h, cudaEventRecord(h->ev_join, sd));
         MSCK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
-        if ((rc = ms_demag_step<Real>(h))) return rc;
-        Bd = (const Real *)h->Bd;
+        if ((rc = ms_demag_step<Real>(h, Bd))) return rc;
         MSCK(h, cudaEventRecord(h->ev_fork, st));
         MSCK(h, cudaStreamWaitEvent(sd, h->ev_fork, 0));
     }
@@ -1759,9 +1803,7 @@ int hamr_ms_set_demag(hamr_ms_t h, int32_t on) {
     MsDeviceGuard dg(h->device);
     if (!h->gtrack.plans) {
         const size_t es = h->prec == HAMR_FP64 ? 8 : 4;
-        MSCK(h, cudaMalloc(&h->Bd, es * 3 * h->P.nc));
         MSCK(h, cudaMalloc(&h->Bfz, es * 3 * h->P.nc));
-        MSCK(h, cudaMemsetAsync(h->Bd, 0, es * 3 * h->P.nc, h->stream));
         const int rc = h->prec == HAMR_FP64 ? demag_grid_setup<double>(h, h->gtrack, h->P.ncx)
                                             : demag_grid_setup<float>(h, h->gtrack, h->P.ncx);
         if (rc) return rc;
