@@ -9,7 +9,8 @@
 //                       column, and the cells' coefficients Ms = Ms0 m_e, A = A0 m_e^2,
 //                       K = K0 m_e^3, alpha = lambda (1 - T / 3 T_C);
 //   3. with Eq. 7     - k_demag_M, in-plane transforms (cuFFT), k_demag_zmul[_r] (the sum
-//                       along z), inverse transforms, k_demag_extract: B_d of the state at t_n;
+//                       along z), inverse transforms: B_d of the state at t_n, which the
+//                       window step and the RK4 stages read from the transform (BdView);
 //   4. k_ms_fused     - the sLLG Heun step of the window (Eq. 1-3), both stages in one pass;
 //                       across the window's x faces a bond sees the direction of the
 //                       micromagnetic cell there;
